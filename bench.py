@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of the sparse All-Pairs self-join on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path over the large sparse workload (n = 200,000
+vectors, m = 100,000 dimensions, power-law |x| with mean 50 and maximum 2,000, Zipf(1.0)
+feature ids, log-normal weights, L2-normalised, t = 0.7): index build from the
+device-resident CSR (statistics, dimension ranks, rank-ordered rows, partial-indexing
+split, posting lists), the join kernel (probe/accumulate, upperbound, dot(x, y'),
+float64 band decisions, compaction) and the output stage that leaves the pairs sorted by
+(i, j) in device memory.
+
+Metric: similarity evaluations per second = n(n-1)/2 pairs decided per step / step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--t 0.7] [--impl aps|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload (the join
+is not sharded across GPUs); the value is all ranks' evaluations / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "similarity evaluations/s"
+UNIT = "pair-evaluations/s"
+WORKLOAD = "large sparse all-pairs: n=200000, m=100000, |x| power law (alpha=1.4135, mean 50, max 2000), Zipf(1.0) ids, log-normal(0,1) weights, L2-normalised, FP32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--t", type=float, default=0.7)
+    ap.add_argument("--impl", default="aps", choices=["aps", "reference"])
+    ap.add_argument("--n", type=int, default=200_000)
+    ap.add_argument("--m", type=int, default=100_000)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=600, help="queries in the oracle's timed sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(n, m, seed=2):
+    import synth
+
+    if n == 200_000 and m == 100_000:
+        return synth.config_large(seed=seed)
+    return synth.config_large(seed=seed, n=n, m=m)
+
+
+# ------------------------------------------------------------------ clocks sampler
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def cpu_baseline(c, t, sample):
+    """The oracle's sequential All-Pairs (all-pairs-2 toggles) on a bounded sample: every
+    vector is indexed, Find-Matches runs for `sample` random queries. Value = similarity
+    evaluations decided by the sampled queries / wall time of the whole call."""
+    import oracle
+
+    rng = np.random.default_rng(123)
+    mask = np.zeros(c.n, np.uint8)
+    mask[rng.choice(c.n, size=min(sample, c.n), replace=False)] = 1
+    t0 = time.perf_counter()
+    pairs, cnt = oracle.all_pairs(c, float(np.float32(t)), oracle.ALL_PAIRS_2, query_mask=mask)
+    dt = time.perf_counter() - t0
+    return {
+        "value": cnt["evaluations"] / dt,
+        "unit": UNIT,
+        "cores": 1,
+        "kind": "oracle",
+        "sample": f"sequential all-pairs-2 (C, FP64) over the full n={c.n} index build, Find-Matches for "
+                  f"{int(mask.sum())} random queries ({cnt['evaluations']} evaluations) in {dt:.2f} s",
+        "seconds": dt,
+    }
+
+
+# ------------------------------------------------------------------ the GPU arm
+def run_aps(args, rank, world):
+    import torch
+
+    import paper_1402_3010_gb300 as aps
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    aps.load()
+    t = float(np.float32(args.t))
+    c = workload(args.n, args.m)
+    stream = torch.cuda.current_stream(dev)
+    ip = torch.from_numpy(c.indptr).to(dev)
+    ix = torch.from_numpy(c.idx).to(dev)
+    vv = torch.from_numpy(c.val).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    evals = c.n * (c.n - 1) // 2
+
+    def step():
+        h = aps.aps_build_index(ip, ix, vv, c.n, c.m, t, 0, stream)
+        p = aps.aps_all_pairs(h)
+        st = aps.aps_index_stats(h)
+        cnt = int(p.count)
+        aps.aps_pairs_free(p)
+        aps.aps_index_free(h)
+        return st, cnt
+
+    # warm-up: also sizes the output staging buffers of later steps through the index hint
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        st, cnt = step()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = Clocks(local)
+    clocks.start()
+    stats = []
+    join_ms = []
+    l0 = aps.aps_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        st, cnt = step()
+        stats.append(st)
+        join_ms.append(st["ms_join"])
+    e1.record(stream)
+    barrier()
+    launches = aps.aps_launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+        hip, hix, hvv = pin(c.indptr), pin(c.idx), pin(c.val)
+        npairs = cnt
+        oi = torch.empty(npairs, dtype=torch.int32).pin_memory()
+        oj = torch.empty(npairs, dtype=torch.int32).pin_memory()
+        os_ = torch.empty(npairs, dtype=torch.float32).pin_memory()
+        hbytes = c.indptr.nbytes + c.idx.nbytes + c.val.nbytes
+
+        def e2e_step():
+            h = aps.aps_build_index(hip.numpy(), hix.numpy(), hvv.numpy(), c.n, c.m, t, 0, stream)
+            p = aps.aps_all_pairs(h)
+            n_out = int(p.count)
+            if n_out <= npairs:
+                aps.aps_pairs_copy_to(p, oi.numpy(), oj.numpy(), os_.numpy(), stream)
+            aps.aps_pairs_free(p)
+            aps.aps_index_free(h)
+            return n_out
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        outs = [e2e_step() for _ in range(args.e2e_steps)]
+        barrier()
+        dt = time.perf_counter() - t0
+        e2e = {"value": world * evals * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": hbytes,
+               "d2h_bytes_per_step": int(max(outs)) * 12, "ms_per_step": 1000 * dt / args.e2e_steps}
+
+    if rank != 0:
+        return None
+    peak, peak_kind = peaks()
+    last = stats[-1]
+    # algorithmic bytes of one join launch: 8 B per posting entry visited, 8 B of (|y'|,
+    # maxweight(y')) per candidate, 16 B per dot(x, y') (row pointer + one prefix entry
+    # per verified candidate, lower bound) and 8 B per staged output pair
+    alg_bytes = 8 * last["visits"] + 8 * last["candidates"] + 16 * last["verified"] + 8 * last["pairs"]
+    jm = statistics.mean(join_ms)
+    achieved = alg_bytes / (jm * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "join_kernel_traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            tr = json.load(f)
+        if tr.get("kernel_version") == "join-v1" and tr.get("t") == t:
+            traffic = tr.get("dram_bytes_per_launch")
+    line = {
+        "metric": METRIC,
+        "value": world * evals * args.steps / (ms * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(args.warmup, 3),
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded generator, no dataset)",
+        "config": {
+            "workload": WORKLOAD,
+            "n": c.n, "m": c.m, "nnz": c.nnz, "t": t,
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "256 MB buffer written between steps (L2 flush)",
+            "pairs_per_step": cnt,
+            "evaluations_per_step": evals,
+        },
+        "roofline": {
+            "bound": "hbm",
+            "kernel": "join_kernel",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": achieved / peak,
+            "peak_kind": peak_kind + " (hbm_gbs, copy bandwidth)",
+            "traffic": traffic,
+            "alg_bytes_per_launch": alg_bytes,
+            "ms_per_launch": jm,
+        },
+        "phases_ms": {"build": last["ms_build"], "join": last["ms_join"], "output": last["ms_sort"],
+                      "join_call": last["ms_total"]},
+        "work": {k: last[k] for k in ("visits", "candidates", "verified", "pairs", "band")},
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(c, t, args.cpu_sample)
+    return line
+
+
+def run_reference(args, rank):
+    """The reference arm: the CPU oracle (no upstream implementation exists), on rank 0."""
+    if rank != 0:
+        return None
+    t = float(np.float32(args.t))
+    c = workload(args.n, args.m)
+    evals, secs = 0, 0.0
+    for _ in range(max(args.warmup, 0)):
+        cpu_baseline(c, t, max(args.cpu_sample // 8, 10))
+    res = []
+    for _ in range(args.steps):
+        r = cpu_baseline(c, t, args.cpu_sample)
+        res.append(r)
+        secs += r["seconds"]
+    value = statistics.mean(r["value"] for r in res)
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1000 * secs / max(args.steps, 1),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": WORKLOAD, "n": c.n, "m": c.m, "nnz": c.nnz, "t": t,
+                   "parallelism": "CPU, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": res[-1]["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        line = run_aps(args, rank, world)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1 and args.impl == "aps":
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

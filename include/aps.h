@@ -1,0 +1,215 @@
+/*
+ * aps.h -- C ABI of the GB300 All-Pairs similarity join library (libaps.so).
+ *
+ * The library finds every pair of unit-norm, non-negative sparse vectors whose inner
+ * product reaches a threshold t (Ozkural & Aykanat, Sec. 2.1: M = {(v_i, v_j) : i != j,
+ * dot(v_i, v_j) >= t}), with the inverted-index All-Pairs method of Sec. 3.2.2
+ * (Alg. 1-2 plus partial indexing, minsize, remscore and upperbound), and a dense
+ * variant for embeddings (the matrix view S = D.D^T of Sec. 2.1) on tensor cores.
+ *
+ * Conventions for every entry point:
+ *   - Plain C types only; no exception crosses the ABI. Every call returns an
+ *     aps_status; on failure aps_last_error() gives a message (thread-local).
+ *   - Input pointers are borrowed for the duration of the call only. Unless the
+ *     APS_DEVICE_PTRS flag is given they are host pointers; with it they must be
+ *     device pointers on the current CUDA device.
+ *   - Objects returned through out-parameters (aps_index, aps_pairs buffers,
+ *     aps_server) are owned by the library and released with the matching *_free.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Calls are synchronous with respect to the host: when they return, results are
+ *     complete (device results are written on `stream`).
+ *   - Vector ids in results are the caller's row numbers. Pairs of a self-join are
+ *     unordered and reported once as (i < j), sorted by (i, j).
+ *   - Scores are float32 within 1e-5 of the float64 dot product of the float32 inputs.
+ *     Pairs whose float32 score lies within a band of t (at least 1e-5 wide) are
+ *     decided by a float64 re-evaluation, so the pair set equals the float64 one.
+ */
+#ifndef APS_H
+#define APS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum aps_status {
+    APS_OK = 0,
+    APS_EINVAL = 1,       /* invalid argument or malformed input */
+    APS_ENOMEM = 2,       /* device or host allocation failed */
+    APS_ECUDA = 3,        /* a CUDA call failed */
+    APS_EOVERFLOW = 4,    /* a caller-sized buffer is too small; count holds the need */
+    APS_EAGAIN = 5,       /* serving: request not finished yet */
+    APS_ETIMEOUT = 6,     /* a bounded device or host wait ran out */
+    APS_ECANCELED = 7,    /* serving: request cancelled or expired */
+    APS_EUNSUPPORTED = 8  /* device or configuration not supported */
+} aps_status;
+
+/* ---- flags ---------------------------------------------------------------------- */
+#define APS_DEVICE_PTRS 0x1u      /* input arrays are device pointers */
+#define APS_NORMALIZE 0x2u        /* L2-normalise rows (float64 norm) instead of checking */
+#define APS_QUERYABLE 0x4u        /* index prefixes split on ||y'||_2 < t so that vectors
+                                     outside the set may query the index (aps_query) */
+#define APS_NO_PARTIAL_INDEX 0x8u /* ablation: index every component (all-pairs-0-array) */
+#define APS_NO_MINSIZE 0x10u      /* ablation: no minsize pruning */
+#define APS_NO_REMSCORE 0x20u     /* ablation: no remscore admission bound */
+#define APS_NO_UPPERBOUND 0x40u   /* ablation: no upperbound before dot(x, y') */
+#define APS_HOST_OUTPUT 0x100u    /* results are copied to pinned host memory */
+
+/* ---- results -------------------------------------------------------------------- */
+typedef struct aps_pairs {
+    int64_t count;   /* number of pairs */
+    int32_t *i;      /* [count] first vector id (self-join: i < j; query: query row) */
+    int32_t *j;      /* [count] second vector id */
+    float *score;    /* [count] float32 score */
+    int32_t on_device; /* 1: the three arrays are device pointers; 0: pinned host memory */
+    int32_t _reserved;
+    void *_priv;     /* library bookkeeping; do not touch */
+} aps_pairs;
+
+/* Work counters and phase times of the last aps_all_pairs / aps_query / batch call on
+ * an index (all counts are exact; times are CUDA-event milliseconds). */
+typedef struct aps_stats {
+    int64_t visits;       /* posting-list entries read in the accumulation loop */
+    int64_t candidates;   /* (x, y) pairs with a non-zero partial score */
+    int64_t verified;     /* candidates that passed upperbound and got dot(x, y') */
+    int64_t pairs;        /* pairs emitted */
+    int64_t band;         /* pairs re-decided in float64 */
+    int64_t evaluations;  /* similarity evaluations decided: sum over instances n(n-1)/2 */
+    int64_t reruns;       /* join re-runs after the output staging buffer grew */
+    float ms_build;       /* index build (aps_build_index / batch) */
+    float ms_join;        /* join kernel launches only (last attempt) */
+    float ms_sort;        /* output stage: count scan + gather into (i, j) order */
+    float ms_total;       /* whole call */
+} aps_stats;
+
+typedef struct aps_index aps_index;
+
+/*
+ * Build the inverted index of n sparse vectors over m dimensions for threshold t
+ * (steps of Alg. 1 plus the all-pairs-1/2 preprocessing of Sec. 3.2.2):
+ *   - per-vector |x| and maxweight(x), per-dimension non-zero counts and maxweight_i(V);
+ *   - dimensions ranked by decreasing non-zero count (ties: ascending id);
+ *   - each vector's components re-ordered by that rank;
+ *   - partial indexing: the leading components whose bound
+ *     b = sum x[i] * maxweight_i(V) stays below t are kept unindexed (x'), the rest go
+ *     into the posting lists (with APS_QUERYABLE the bound is ||x'||_2 instead);
+ *   - posting lists I_d of (vector id, weight).
+ * Input: CSR with int64 indptr[n+1] (indptr[0] = 0), int32 idx[nnz] strictly increasing
+ * within each row and in [0, m), float32 val[nnz] finite and > 0. Each row must have
+ * L2 norm within 1e-3 of 1 unless APS_NORMALIZE is given. Empty rows are legal (they
+ * match nothing). 0 < t <= 1. n >= 0, m >= 1, nnz < 2^31.
+ * Errors: APS_EINVAL (message names the first offending row), APS_ENOMEM, APS_ECUDA.
+ */
+aps_status aps_build_index(const int64_t *indptr, const int32_t *idx, const float *val,
+                           int32_t n, int32_t m, float t, uint32_t flags, void *stream,
+                           aps_index **out);
+
+/* Self-join of the indexed set at the build threshold: every pair (i < j) with
+ * dot >= t (Alg. 1-2 with the all-pairs-2 bounds), sorted by (i, j).
+ * flags: APS_NO_MINSIZE / APS_NO_REMSCORE / APS_NO_UPPERBOUND ablations and
+ * APS_HOST_OUTPUT. Result buffers are allocated by the library; free with aps_pairs_free. */
+aps_status aps_all_pairs(aps_index *index, uint32_t flags, aps_pairs *out);
+
+/* Match nq external query vectors (CSR as in aps_build_index) against the index
+ * (the local matching step of the horizontal algorithm, Alg. 6): every (q, y) with
+ * dot(q, y) >= t, as i = query row, j = vector id, sorted by (i, j). The index must
+ * have been built with APS_QUERYABLE, and t >= the build threshold. */
+aps_status aps_query(aps_index *index, const int64_t *qptr, const int32_t *qidx,
+                     const float *qval, int32_t nq, float t, uint32_t flags, aps_pairs *out);
+
+/* Read back the index build results for verification of each step. Any pointer may be
+ * NULL. Host arrays, caller-allocated, sizes: len/mw/split/qsplit/mw_pre [n],
+ * rank_of_dim/nnz_d/mw_d [m], crank/cval [nnz] (components re-ordered by rank, the
+ * CSR row pointers are the input's), list_ptr [m+1] (by rank), post_id/post_w [list_ptr[m]]. */
+aps_status aps_index_export(const aps_index *index, int32_t *len, float *mw, int32_t *nnz_d,
+                            float *mw_d, int32_t *rank_of_dim, int32_t *crank, float *cval,
+                            int32_t *split, int32_t *qsplit, float *mw_pre, int64_t *list_ptr,
+                            int32_t *post_id, float *post_w);
+
+/* Sizes of the index: n, m, nnz and the number of indexed components. */
+aps_status aps_index_info(const aps_index *index, int32_t *n, int32_t *m, int64_t *nnz,
+                          int64_t *indexed);
+
+/* Counters and timings of the last join on this index (see aps_stats). */
+aps_status aps_index_stats(const aps_index *index, aps_stats *out);
+
+void aps_index_free(aps_index *index);
+
+/* Release the buffers of a result (device or host). Safe on a zeroed aps_pairs. */
+void aps_pairs_free(aps_pairs *pairs);
+
+/* Copy a result's arrays into caller-owned buffers (host or device; any may be NULL) on
+ * `stream`, and wait for the copies. */
+aps_status aps_pairs_copy_to(const aps_pairs *pairs, int32_t *i, int32_t *j, float *score,
+                             void *stream);
+
+/* ---- batched form --------------------------------------------------------------- */
+typedef struct aps_instance {
+    const int64_t *indptr; /* CSR of one instance, as in aps_build_index */
+    const int32_t *idx;
+    const float *val;
+    int32_t n, m;
+    float t;
+    int32_t _reserved;
+} aps_instance;
+
+/* Self-join of k independent instances in one pass: all instances are indexed by one
+ * set of kernels and joined by one persistent launch per size class. outs[k] receives
+ * instance k's pairs (i < j, local row ids, sorted); all k results share one allocation,
+ * released by calling aps_pairs_free on every element. stats (may be NULL) gets the
+ * totals. */
+aps_status aps_batch_all_pairs(int32_t k, const aps_instance *inst, uint32_t flags,
+                               void *stream, aps_pairs *outs, aps_stats *stats);
+
+/* ---- dense embeddings ----------------------------------------------------------- */
+/* All pairs (i < j) of n unit vectors X[n, d] (float32, row-major) with X_i . X_j >= t:
+ * the S = D.D^T view of Sec. 2.1 computed as a BF16 tensor-core product with float32
+ * accumulation, a provable margin delta below t for candidates, float32 rescoring of
+ * the candidates from X, float64 inside the band, sorted by (i, j). d must be a
+ * multiple of 64 and at most 512. Needs an sm_103a device. */
+aps_status aps_all_pairs_dense(const float *X, int32_t n, int32_t d, float t, uint32_t flags,
+                               void *stream, aps_pairs *out, aps_stats *stats);
+
+/* ---- serving -------------------------------------------------------------------- */
+typedef struct aps_server aps_server;
+
+typedef struct aps_query_req {
+    const int64_t *qptr; /* host CSR of a query batch (copied at submit) */
+    const int32_t *qidx;
+    const float *qval;
+    int32_t nq;
+    float t;             /* >= the index build threshold */
+} aps_query_req;
+
+/* A request loop over a device-resident APS_QUERYABLE index. Submitted query batches
+ * are admitted in arrival order when one of `slots` execution slots is free and their
+ * estimated device footprint fits in mem_budget bytes; admitted batches run
+ * concurrently on separate streams (continuous batching). */
+aps_status aps_server_create(aps_index *index, size_t mem_budget, int32_t slots,
+                             aps_server **out);
+aps_status aps_stream_submit(aps_server *server, const aps_query_req *req, uint64_t *ticket);
+/* Wait up to timeout_us (0 = just check) for a ticket. APS_EAGAIN if not done yet; on
+ * APS_OK `out` receives the pairs (host memory) and the ticket is retired. */
+aps_status aps_stream_poll(aps_server *server, uint64_t ticket, int32_t timeout_us,
+                           aps_pairs *out);
+aps_status aps_stream_cancel(aps_server *server, uint64_t ticket);
+void aps_server_free(aps_server *server);
+
+/* ---- misc ----------------------------------------------------------------------- */
+const char *aps_last_error(void);
+const char *aps_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all devices). */
+int64_t aps_launch_count(void);
+
+/* Test hook: make the k-th next device allocation of the library fail with APS_ENOMEM
+ * (k >= 1; 0 disables). Host-side only; no GPU fault is involved. */
+void aps_debug_fail_alloc(int64_t k);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APS_H */

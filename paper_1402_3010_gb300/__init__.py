@@ -1,0 +1,355 @@
+"""Python binding of libaps.so, the GB300 All-Pairs similarity join (C ABI in include/aps.h).
+
+Argument marshalling only: every step of the join runs in the library's CUDA kernels.
+Functions keep the C names. Host inputs are NumPy arrays; device inputs are PyTorch CUDA
+tensors (PyTorch is used for device memory and streams only). If the compiled library
+is missing this module raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "APSError", "load", "lib_path",
+    "aps_build_index", "aps_all_pairs", "aps_query", "aps_index_export", "aps_index_info",
+    "aps_index_stats", "aps_index_free", "aps_pairs_free", "aps_pairs_copy_to",
+    "aps_batch_all_pairs", "aps_all_pairs_dense", "aps_server_create", "aps_stream_submit",
+    "aps_stream_poll", "aps_stream_cancel", "aps_server_free", "aps_last_error", "aps_version",
+    "aps_debug_fail_alloc", "aps_launch_count", "pairs_to_numpy", "pairs_to_torch",
+    "DEVICE_PTRS", "NORMALIZE", "QUERYABLE", "NO_PARTIAL_INDEX", "NO_MINSIZE", "NO_REMSCORE",
+    "NO_UPPERBOUND", "HOST_OUTPUT",
+]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libaps.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, EAGAIN, ETIMEOUT, ECANCELED, EUNSUPPORTED = range(9)
+STATUS_NAMES = ["APS_OK", "APS_EINVAL", "APS_ENOMEM", "APS_ECUDA", "APS_EOVERFLOW", "APS_EAGAIN",
+                "APS_ETIMEOUT", "APS_ECANCELED", "APS_EUNSUPPORTED"]
+
+DEVICE_PTRS = 0x1
+NORMALIZE = 0x2
+QUERYABLE = 0x4
+NO_PARTIAL_INDEX = 0x8
+NO_MINSIZE = 0x10
+NO_REMSCORE = 0x20
+NO_UPPERBOUND = 0x40
+HOST_OUTPUT = 0x100
+
+_P = ctypes.c_void_p
+_i32, _i64, _u32, _u64, _f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_float
+
+
+class aps_pairs(ctypes.Structure):
+    _fields_ = [("count", _i64), ("i", _P), ("j", _P), ("score", _P), ("on_device", _i32),
+                ("_reserved", _i32), ("_priv", _P)]
+
+
+class aps_stats(ctypes.Structure):
+    _fields_ = [("visits", _i64), ("candidates", _i64), ("verified", _i64), ("pairs", _i64),
+                ("band", _i64), ("evaluations", _i64), ("reruns", _i64), ("ms_build", _f32),
+                ("ms_join", _f32), ("ms_sort", _f32), ("ms_total", _f32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class aps_instance(ctypes.Structure):
+    _fields_ = [("indptr", _P), ("idx", _P), ("val", _P), ("n", _i32), ("m", _i32), ("t", _f32),
+                ("_reserved", _i32)]
+
+
+class aps_query_req(ctypes.Structure):
+    _fields_ = [("qptr", _P), ("qidx", _P), ("qval", _P), ("nq", _i32), ("t", _f32)]
+
+
+class APSError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{where}: {name}: {aps_last_error()}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libaps.so (built by __graft_entry__.build() or paper_1402_3010_gb300._build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(
+                f"{_LIB_PATH} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(_LIB_PATH)
+        sigs = {
+            "aps_build_index": (_i32, [_P, _P, _P, _i32, _i32, _f32, _u32, _P, ctypes.POINTER(_P)]),
+            "aps_all_pairs": (_i32, [_P, _u32, ctypes.POINTER(aps_pairs)]),
+            "aps_query": (_i32, [_P, _P, _P, _P, _i32, _f32, _u32, ctypes.POINTER(aps_pairs)]),
+            "aps_index_export": (_i32, [_P] + [_P] * 13),
+            "aps_index_info": (_i32, [_P, _P, _P, _P, _P]),
+            "aps_index_stats": (_i32, [_P, ctypes.POINTER(aps_stats)]),
+            "aps_index_free": (None, [_P]),
+            "aps_pairs_free": (None, [ctypes.POINTER(aps_pairs)]),
+            "aps_pairs_copy_to": (_i32, [ctypes.POINTER(aps_pairs), _P, _P, _P, _P]),
+            "aps_batch_all_pairs": (_i32, [_i32, ctypes.POINTER(aps_instance), _u32, _P,
+                                           ctypes.POINTER(aps_pairs), ctypes.POINTER(aps_stats)]),
+            "aps_all_pairs_dense": (_i32, [_P, _i32, _i32, _f32, _u32, _P, ctypes.POINTER(aps_pairs),
+                                           ctypes.POINTER(aps_stats)]),
+            "aps_server_create": (_i32, [_P, ctypes.c_size_t, _i32, ctypes.POINTER(_P)]),
+            "aps_stream_submit": (_i32, [_P, ctypes.POINTER(aps_query_req), ctypes.POINTER(_u64)]),
+            "aps_stream_poll": (_i32, [_P, _u64, _i32, ctypes.POINTER(aps_pairs)]),
+            "aps_stream_cancel": (_i32, [_P, _u64]),
+            "aps_server_free": (None, [_P]),
+            "aps_last_error": (ctypes.c_char_p, []),
+            "aps_version": (ctypes.c_char_p, []),
+            "aps_debug_fail_alloc": (None, [_i64]),
+            "aps_launch_count": (_i64, []),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def aps_last_error() -> str:
+    if _lib is None:
+        return ""
+    v = _lib.aps_last_error()
+    return v.decode() if v else ""
+
+
+def aps_version() -> str:
+    return load().aps_version().decode()
+
+
+def aps_launch_count() -> int:
+    return int(load().aps_launch_count())
+
+
+def aps_debug_fail_alloc(k: int) -> None:
+    load().aps_debug_fail_alloc(int(k))
+
+
+def _check(st: int, where: str):
+    if st != OK:
+        raise APSError(st, where)
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _csr_args(indptr, idx, val):
+    """(pointers, flags, keep-alive) for host NumPy or device torch CSR arrays."""
+    if _is_torch(indptr):
+        for a, dt in ((indptr, "int64"), (idx, "int32"), (val, "float32")):
+            if not a.is_cuda or str(a.dtype) != f"torch.{dt}" or not a.is_contiguous():
+                raise TypeError(f"device CSR arrays must be contiguous CUDA {dt} tensors")
+        return (_ptr(indptr), _ptr(idx), _ptr(val)), DEVICE_PTRS, (indptr, idx, val)
+    ip = np.ascontiguousarray(indptr, dtype=np.int64)
+    ix = np.ascontiguousarray(idx, dtype=np.int32)
+    vv = np.ascontiguousarray(val, dtype=np.float32)
+    return (ip.ctypes.data, ix.ctypes.data, vv.ctypes.data), 0, (ip, ix, vv)
+
+
+def aps_build_index(indptr, idx, val, n: int, m: int, t: float, flags: int = 0, stream=None) -> int:
+    """Build the index; returns an opaque handle (int). Free with aps_index_free."""
+    lib = load()
+    (p0, p1, p2), f, keep = _csr_args(indptr, idx, val)
+    out = _P()
+    st = lib.aps_build_index(p0, p1, p2, int(n), int(m), float(t), int(flags) | f, _stream_ptr(stream),
+                             ctypes.byref(out))
+    del keep
+    _check(st, "aps_build_index")
+    return out.value
+
+
+def aps_all_pairs(index: int, flags: int = 0) -> aps_pairs:
+    lib = load()
+    out = aps_pairs()
+    _check(lib.aps_all_pairs(index, int(flags), ctypes.byref(out)), "aps_all_pairs")
+    return out
+
+
+def aps_query(index: int, qptr, qidx, qval, nq: int, t: float, flags: int = 0) -> aps_pairs:
+    lib = load()
+    (p0, p1, p2), f, keep = _csr_args(qptr, qidx, qval)
+    out = aps_pairs()
+    st = lib.aps_query(index, p0, p1, p2, int(nq), float(t), int(flags) | f, ctypes.byref(out))
+    del keep
+    _check(st, "aps_query")
+    return out
+
+
+def aps_index_info(index: int) -> dict:
+    lib = load()
+    n, m, nnz, ind = _i32(), _i32(), _i64(), _i64()
+    _check(lib.aps_index_info(index, ctypes.byref(n), ctypes.byref(m), ctypes.byref(nnz), ctypes.byref(ind)),
+           "aps_index_info")
+    return {"n": n.value, "m": m.value, "nnz": nnz.value, "indexed": ind.value}
+
+
+def aps_index_export(index: int) -> dict:
+    info = aps_index_info(index)
+    n, m, nnz, nsuf = info["n"], info["m"], info["nnz"], info["indexed"]
+    out = {
+        "len": np.empty(n, np.int32), "mw": np.empty(n, np.float32), "nnz_d": np.empty(m, np.int32),
+        "mw_d": np.empty(m, np.float32), "rank_of_dim": np.empty(m, np.int32),
+        "crank": np.empty(nnz, np.int32), "cval": np.empty(nnz, np.float32), "split": np.empty(n, np.int32),
+        "qsplit": np.empty(n, np.int32), "mw_pre": np.empty(n, np.float32), "list_ptr": np.empty(m + 1, np.int64),
+        "post_id": np.empty(nsuf, np.int32), "post_w": np.empty(nsuf, np.float32),
+    }
+    order = ["len", "mw", "nnz_d", "mw_d", "rank_of_dim", "crank", "cval", "split", "qsplit", "mw_pre",
+             "list_ptr", "post_id", "post_w"]
+    _check(load().aps_index_export(index, *[out[k].ctypes.data for k in order]), "aps_index_export")
+    return out
+
+
+def aps_index_stats(index: int) -> dict:
+    s = aps_stats()
+    _check(load().aps_index_stats(index, ctypes.byref(s)), "aps_index_stats")
+    return s.as_dict()
+
+
+def aps_index_free(index: int) -> None:
+    if index:
+        load().aps_index_free(index)
+
+
+def aps_pairs_free(p: aps_pairs) -> None:
+    load().aps_pairs_free(ctypes.byref(p))
+
+
+def aps_pairs_copy_to(p: aps_pairs, i, j, score, stream=None) -> None:
+    _check(load().aps_pairs_copy_to(ctypes.byref(p), _ptr(i), _ptr(j), _ptr(score), _stream_ptr(stream)),
+           "aps_pairs_copy_to")
+
+
+def pairs_to_numpy(p: aps_pairs):
+    """(i, j, score) NumPy copies of a result."""
+    n = int(p.count)
+    i = np.empty(n, np.int32)
+    j = np.empty(n, np.int32)
+    s = np.empty(n, np.float32)
+    if n:
+        aps_pairs_copy_to(p, i, j, s)
+    return i, j, s
+
+
+def pairs_to_torch(p: aps_pairs, device="cuda"):
+    """(i, j, score) torch CUDA tensors copied from a result."""
+    import torch
+
+    n = int(p.count)
+    i = torch.empty(n, dtype=torch.int32, device=device)
+    j = torch.empty(n, dtype=torch.int32, device=device)
+    s = torch.empty(n, dtype=torch.float32, device=device)
+    if n:
+        aps_pairs_copy_to(p, i, j, s, torch.cuda.current_stream(device))
+    return i, j, s
+
+
+def aps_batch_all_pairs(instances, flags: int = 0, stream=None):
+    """instances: list of (indptr, idx, val, n, m, t) (NumPy host or torch device arrays).
+    Returns (list of aps_pairs, stats dict)."""
+    lib = load()
+    k = len(instances)
+    arr = (aps_instance * k)()
+    keep = []
+    f = 0
+    for a, (ip, ix, vv, n, m, t) in enumerate(instances):
+        (p0, p1, p2), f, kp = _csr_args(ip, ix, vv)
+        keep.append(kp)
+        arr[a].indptr, arr[a].idx, arr[a].val = p0, p1, p2
+        arr[a].n, arr[a].m, arr[a].t = int(n), int(m), float(t)
+    outs = (aps_pairs * k)()
+    st = aps_stats()
+    rc = lib.aps_batch_all_pairs(k, arr, int(flags) | f, _stream_ptr(stream), outs, ctypes.byref(st))
+    del keep
+    _check(rc, "aps_batch_all_pairs")
+    return list(outs), st.as_dict()
+
+
+def aps_all_pairs_dense(X, t: float, flags: int = 0, stream=None):
+    """X: float32 [n, d] NumPy (host) or torch CUDA tensor. Returns (aps_pairs, stats dict)."""
+    lib = load()
+    if _is_torch(X):
+        if not X.is_cuda or str(X.dtype) != "torch.float32" or not X.is_contiguous():
+            raise TypeError("X must be a contiguous CUDA float32 tensor")
+        f = DEVICE_PTRS
+        ptr = X.data_ptr()
+    else:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        f = 0
+        ptr = X.ctypes.data
+    n, d = X.shape
+    out = aps_pairs()
+    st = aps_stats()
+    _check(lib.aps_all_pairs_dense(ptr, int(n), int(d), float(t), int(flags) | f, _stream_ptr(stream),
+                                   ctypes.byref(out), ctypes.byref(st)), "aps_all_pairs_dense")
+    return out, st.as_dict()
+
+
+def aps_server_create(index: int, mem_budget: int, slots: int) -> int:
+    out = _P()
+    _check(load().aps_server_create(index, int(mem_budget), int(slots), ctypes.byref(out)), "aps_server_create")
+    return out.value
+
+
+def aps_stream_submit(server: int, qptr, qidx, qval, nq: int, t: float) -> int:
+    ip = np.ascontiguousarray(qptr, dtype=np.int64)
+    ix = np.ascontiguousarray(qidx, dtype=np.int32)
+    vv = np.ascontiguousarray(qval, dtype=np.float32)
+    req = aps_query_req(ip.ctypes.data, ix.ctypes.data, vv.ctypes.data, int(nq), float(t))
+    ticket = _u64()
+    _check(load().aps_stream_submit(server, ctypes.byref(req), ctypes.byref(ticket)), "aps_stream_submit")
+    return ticket.value
+
+
+def aps_stream_poll(server: int, ticket: int, timeout_us: int = 0):
+    """Returns aps_pairs when done, None while the request is still running."""
+    out = aps_pairs()
+    st = load().aps_stream_poll(server, int(ticket), int(timeout_us), ctypes.byref(out))
+    if st == EAGAIN:
+        return None
+    _check(st, "aps_stream_poll")
+    return out
+
+
+def aps_stream_cancel(server: int, ticket: int) -> None:
+    _check(load().aps_stream_cancel(server, int(ticket)), "aps_stream_cancel")
+
+
+def aps_server_free(server: int) -> None:
+    if server:
+        load().aps_server_free(server)

@@ -1,0 +1,500 @@
+// Index build: input statistics, dimension ranking, canonical rows, partial-indexing
+// split and the suffix inverted index (the preprocessing of all-pairs-1/2 and the
+// index-insertion step of Alg. 1, done for all vectors at once).
+#include <algorithm>
+#include <cmath>
+
+#include "index.cuh"
+
+namespace aps {
+namespace {
+
+constexpr int T256 = 256;
+
+__device__ __forceinline__ int inst_of_vec(const InstDesc *inst, int k, int64_t x) {
+    // last instance whose vbase <= x (instances with n == 0 share the next vbase)
+    int lo = 0, hi = k;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (inst[mid].vbase <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo - 1;
+}
+
+__device__ __forceinline__ int inst_of_rank(const InstDesc *inst, int k, int64_t r) {
+    int lo = 0, hi = k;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((int64_t)inst[mid].rbase <= r) lo = mid + 1; else hi = mid;
+    }
+    return lo - 1;
+}
+
+__global__ void k_vinst(const InstDesc *inst, int k, int64_t N, int32_t *vinst) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += (int64_t)gridDim.x * blockDim.x)
+        vinst[x] = inst_of_vec(inst, k, x);
+}
+
+// Validation codes reported as (row << 8 | code) through atomicMin.
+enum { E_PTR = 1, E_IDX_RANGE = 2, E_IDX_ORDER = 3, E_VALUE = 4, E_NORM = 5 };
+
+// One thread per row: checks the row, records |x| and maxweight(x), and copies the values
+// (scaled to unit norm with APS_NORMALIZE).
+__global__ void k_validate(const int64_t *__restrict__ indptr, const int32_t *__restrict__ idx,
+                           const float *__restrict__ val, const int32_t *__restrict__ vinst,
+                           const InstDesc *__restrict__ inst, int64_t N, int64_t nnz, uint32_t flags,
+                           int32_t *__restrict__ erow, float *__restrict__ vout, int32_t *__restrict__ len,
+                           float *__restrict__ mw, unsigned long long *err) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = indptr[x], b = indptr[x + 1];
+        if (a < 0 || b < a || b > nnz) {
+            atomicMin(err, ((unsigned long long)x << 8) | E_PTR);
+            len[x] = 0;
+            mw[x] = 0.f;
+            continue;
+        }
+        int m = inst[vinst[x]].m;
+        int prev = -1;
+        int code = 0;
+        double ss = 0.0;
+        for (int64_t p = a; p < b; p++) {
+            int d = idx[p];
+            float v = val[p];
+            if (d < 0 || d >= m) code = code ? code : E_IDX_RANGE;
+            else if (d <= prev) code = code ? code : E_IDX_ORDER;
+            if (!(v > 0.f) || !isfinite(v)) code = code ? code : E_VALUE;
+            prev = d;
+            ss += (double)v * (double)v;
+            erow[p] = (int32_t)x;
+        }
+        float best = 0.f;
+        if (b > a && !code) {
+            double nrm = sqrt(ss);
+            if (flags & APS_NORMALIZE) {
+                for (int64_t p = a; p < b; p++) {
+                    float v = (float)((double)val[p] / nrm);
+                    vout[p] = v;
+                    best = fmaxf(best, v);
+                }
+            } else {
+                if (fabs(nrm - 1.0) > 1e-3) code = E_NORM;
+                for (int64_t p = a; p < b; p++) {
+                    vout[p] = val[p];
+                    best = fmaxf(best, val[p]);
+                }
+            }
+        }
+        if (code) atomicMin(err, ((unsigned long long)x << 8) | (unsigned long long)code);
+        len[x] = (int32_t)(b - a);
+        mw[x] = best;
+    }
+}
+
+// Per-dimension non-zero count and maxweight_i(V) (positive floats order like ints).
+__global__ void k_dimstats(const int32_t *__restrict__ idx, const float *__restrict__ vout,
+                           const int32_t *__restrict__ erow, const int32_t *__restrict__ vinst,
+                           const InstDesc *__restrict__ inst, int64_t nnz, int32_t *nnz_d, float *mw_d) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t D = (int64_t)inst[vinst[erow[p]]].rbase + idx[p];
+        atomicAdd(&nnz_d[D], 1);
+        atomicMax(reinterpret_cast<int *>(&mw_d[D]), __float_as_int(vout[p]));
+    }
+}
+
+// Dimension order of all-pairs-1: decreasing non-zero count; the sort is stable and the
+// input is in id order, so ties keep ascending dimension id.
+__global__ void k_rank_keys(const int32_t *__restrict__ nnz_d, const InstDesc *__restrict__ inst, int k,
+                            int64_t M, int nbits, uint64_t nmax, uint64_t *keys, uint32_t *vals) {
+    for (int64_t D = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; D < M; D += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t ki = (uint64_t)inst_of_rank(inst, k, D);
+        keys[D] = (ki << nbits) | (nmax - (uint64_t)nnz_d[D]);
+        vals[D] = (uint32_t)D;
+    }
+}
+
+__global__ void k_rank_scatter(const uint32_t *__restrict__ vals, const InstDesc *__restrict__ inst, int k,
+                               int64_t M, const float *__restrict__ mw_d, int32_t *rank_of_dim,
+                               int32_t *dim_of_rank, float *mwr) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t D = vals[i];
+        int ki = inst_of_rank(inst, k, i);
+        rank_of_dim[D] = (int32_t)(i - inst[ki].rbase);
+        dim_of_rank[i] = (int32_t)D;
+        mwr[i] = mw_d[D];
+    }
+}
+
+__global__ void k_canon_keys(const int32_t *__restrict__ idx, const int32_t *__restrict__ erow,
+                             const int32_t *__restrict__ vinst, const InstDesc *__restrict__ inst,
+                             const int32_t *__restrict__ rank_of_dim, int64_t nnz, int rb, uint64_t *keys,
+                             uint32_t *vals) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t x = erow[p];
+        int32_t r = rank_of_dim[(int64_t)inst[vinst[x]].rbase + idx[p]];
+        keys[p] = ((uint64_t)x << rb) | (uint64_t)r;
+        vals[p] = (uint32_t)p;
+    }
+}
+
+__global__ void k_canon_gather(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                               const float *__restrict__ vout, int64_t nnz, uint64_t rmask, int32_t *crank,
+                               float *cval) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
+        crank[q] = (int32_t)(keys[q] & rmask);
+        cval[q] = vout[vals[q]];
+    }
+}
+
+// Partial indexing (all-pairs-1): walking x's components in rank order, b accumulates
+// x[i] * maxweight_i(V) in float64; qsplit = the first component where b >= t (the
+// remscore boundary for x as a query). The index split is qsplit, or 0 without partial
+// indexing, or, for a queryable index, the first component where ||x_prefix||_2 reaches
+// t (with a margin for the 1e-3 norm tolerance).
+__global__ void k_split(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
+                        const float *__restrict__ cval, const float *__restrict__ mwr,
+                        const int32_t *__restrict__ vinst, const InstDesc *__restrict__ inst, int64_t N,
+                        uint32_t flags, int32_t *split, int32_t *qsplit, float *mwpre) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += (int64_t)gridDim.x * blockDim.x) {
+        const InstDesc I = inst[vinst[x]];
+        const double t = (double)I.t;
+        int64_t a = cptr[x], b = cptr[x + 1];
+        int32_t L = (int32_t)(b - a);
+        int32_t qs = L, cs = L;
+        double bmw = 0.0, ss = 0.0;
+        for (int64_t p = a; p < b; p++) {
+            double v = (double)cval[p];
+            bmw += v * (double)mwr[(int64_t)I.rbase + crank[p]];
+            ss += v * v;
+            if (qs == L && bmw >= t) qs = (int32_t)(p - a);
+            if (cs == L && ss * (1.0 + 2e-3) >= t * t) cs = (int32_t)(p - a);
+            if (qs < L && cs < L) break;
+        }
+        int32_t sp = (flags & APS_NO_PARTIAL_INDEX) ? 0 : ((flags & APS_QUERYABLE) ? cs : qs);
+        float best = 0.f;
+        for (int64_t p = a; p < a + sp; p++) best = fmaxf(best, cval[p]);
+        split[x] = sp;
+        qsplit[x] = qs;
+        mwpre[x] = best;
+    }
+}
+
+// Suffix entries get their posting order key (global rank, window, decreasing |y|); the
+// unindexed prefix entries get a sentinel rank past the end so they sort last.
+__global__ void k_post_keys(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
+                            const int32_t *__restrict__ erow, const int32_t *__restrict__ split,
+                            const int32_t *__restrict__ len, const int32_t *__restrict__ vinst,
+                            const InstDesc *__restrict__ inst, int64_t nnz, int64_t M, int wb,
+                            uint64_t *keys, uint32_t *vals, unsigned long long *nsuf) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t x = erow[p];
+        const InstDesc &I = inst[vinst[x]];
+        bool suf = (p - cptr[x]) >= split[x];
+        uint64_t key;
+        if (suf) {
+            uint64_t R = (uint64_t)I.rbase + (uint64_t)crank[p];
+            uint64_t w = (uint64_t)((x - I.vbase) / I.W);
+            uint64_t lk = 65535u - (uint64_t)min(len[x], 65535);
+            key = (R << (wb + 16)) | (w << 16) | lk;
+            atomicAdd(nsuf, 1ull);
+        } else {
+            key = (uint64_t)M << (wb + 16);
+        }
+        keys[p] = key;
+        vals[p] = (uint32_t)p;
+    }
+}
+
+__global__ void k_post_fill(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                            const int32_t *__restrict__ erow, const float *__restrict__ cval,
+                            const int32_t *__restrict__ vinst, const InstDesc *__restrict__ inst, int k,
+                            int64_t nsuf, int wb, int2 *post, int32_t *lcount, int32_t *wcount) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nsuf; q += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t p = vals[q];
+        int64_t x = erow[p];
+        const InstDesc &I = inst[vinst[x]];
+        post[q] = make_int2((int32_t)(x - I.vbase), __float_as_int(cval[p]));
+        int64_t R = (int64_t)(keys[q] >> (wb + 16));
+        atomicAdd(&lcount[R], 1);
+        if (I.nw > 1) {
+            int64_t w = (int64_t)((keys[q] >> 16) & ((1ull << wb) - 1));
+            atomicAdd(&wcount[I.wbase + (R - I.rbase) * (I.nw + 1) + w], 1);
+        }
+    }
+}
+
+// Window offsets inside each list of a multi-window instance: in-place exclusive scan of
+// the per-window counts of one rank.
+__global__ void k_wptr_scan(const InstDesc *__restrict__ inst, int k, int64_t M, int32_t *wptr) {
+    for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R < M; R += (int64_t)gridDim.x * blockDim.x) {
+        const InstDesc &I = inst[inst_of_rank(inst, k, R)];
+        if (I.nw <= 1) continue;
+        int32_t *w = wptr + I.wbase + (R - I.rbase) * (I.nw + 1);
+        int32_t acc = 0;
+        for (int i = 0; i <= I.nw; i++) {
+            int32_t c = w[i];
+            w[i] = acc;
+            acc += c;
+        }
+    }
+}
+
+// Join work list: every vector with later candidates in its instance, keyed by
+// (size class, decreasing estimated cost) so that the persistent join takes the most
+// expensive queries first (least-loaded-first idea of the vertical algorithm's binning).
+__global__ void k_item_keys(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
+                            const int64_t *__restrict__ lptr, const int32_t *__restrict__ vinst,
+                            const InstDesc *__restrict__ inst, int64_t N, uint64_t *keys, uint32_t *vals,
+                            unsigned long long *class_count) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += (int64_t)gridDim.x * blockDim.x) {
+        const InstDesc &I = inst[vinst[x]];
+        int64_t lx = x - I.vbase;
+        uint64_t key;
+        if (lx < (int64_t)I.n - 1) {
+            double later = (double)(I.n - 1 - lx);
+            double lists = 0.0;
+            for (int64_t p = cptr[x]; p < cptr[x + 1]; p++) {
+                int64_t R = (int64_t)I.rbase + crank[p];
+                lists += (double)(lptr[R + 1] - lptr[R]);
+            }
+            double cost = lists * later / (double)I.n + later / 8.0 + 32.0;
+            uint64_t c = cost >= 4294967295.0 ? 0xffffffffull : (uint64_t)cost;
+            int cls = I.G == 1 ? 0 : I.G == 2 ? 1 : I.G == 4 ? 2 : 3;
+            key = ((uint64_t)cls << 32) | (0xffffffffull - c);
+            atomicAdd(&class_count[cls], 1ull);
+        } else {
+            key = 4ull << 32;
+        }
+        keys[x] = key;
+        vals[x] = (uint32_t)x;
+    }
+}
+
+__global__ void k_take_vals(const uint32_t *__restrict__ vals, int64_t n, int32_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)vals[i];
+}
+
+const char *code_name(int c) {
+    switch (c) {
+        case E_PTR: return "row pointers decrease or exceed nnz";
+        case E_IDX_RANGE: return "dimension index out of [0, m)";
+        case E_IDX_ORDER: return "dimension indices not strictly increasing";
+        case E_VALUE: return "value not finite and > 0";
+        case E_NORM: return "row L2 norm differs from 1 by more than 1e-3 (pass APS_NORMALIZE)";
+        default: return "invalid input";
+    }
+}
+
+}  // namespace
+
+aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_t *idx, const float *val,
+                              const std::vector<InstDesc> &inst_in, cudaStream_t s) {
+    const int k = (int)inst_in.size();
+    ix->k = k;
+    ix->stream = s;
+    // ---- host-side layout of instances: ranks, windows, classes
+    std::vector<InstDesc> inst = inst_in;
+    int64_t N = 0, M = 0, nqw = 0, nwptr = 0;
+    int32_t maxm = 1, maxn = 1, maxnw = 1;
+    for (int i = 0; i < k; i++) {
+        InstDesc &I = inst[i];
+        I.vbase = N;
+        I.rbase = (int32_t)M;
+        if (I.n <= JOIN_WMAX / 8) { I.G = 8; I.W = JOIN_WMAX / 8; }
+        else if (I.n <= JOIN_WMAX / 4) { I.G = 4; I.W = JOIN_WMAX / 4; }
+        else if (I.n <= JOIN_WMAX / 2) { I.G = 2; I.W = JOIN_WMAX / 2; }
+        else { I.G = 1; I.W = JOIN_WMAX; }
+        I.nw = I.n > 0 ? (int32_t)((I.n + I.W - 1) / I.W) : 0;
+        I.qwbase = nqw;
+        I.wbase = nwptr;
+        nqw += (int64_t)I.n * I.nw;
+        if (I.nw > 1) nwptr += (int64_t)I.m * (I.nw + 1);
+        N += I.n;
+        M += I.m;
+        maxm = std::max(maxm, I.m);
+        maxn = std::max(maxn, I.n);
+        maxnw = std::max(maxnw, I.nw);
+    }
+    if (M >= (1ll << 31) || N >= (1ll << 31)) {
+        set_error("too many vectors or dimensions (limit 2^31 - 1)");
+        return APS_EINVAL;
+    }
+    ix->N = N;
+    ix->M = M;
+    ix->nqw = nqw;
+    ix->nwptr = nwptr;
+    ix->maxm = maxm;
+    ix->inst_h = inst;
+    IndexArrays &d = ix->d;
+
+    int64_t nnz = 0;
+    APS_CUDA(cudaMemcpyAsync(&nnz, indptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    int64_t first = 0;
+    APS_CUDA(cudaMemcpyAsync(&first, indptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    APS_CUDA(cudaStreamSynchronize(s));
+    if (first != 0 || nnz < 0 || nnz >= (1ll << 31)) {
+        set_error("indptr[0] must be 0 and nnz in [0, 2^31); got indptr[0]=%lld nnz=%lld",
+                  (long long)first, (long long)nnz);
+        return APS_EINVAL;
+    }
+    ix->nnz = nnz;
+    for (int i = 0; i < k; i++) inst[i].ebase = 0;
+
+    APS_TRY(d.inst.alloc((size_t)k, s));
+    APS_CUDA(cudaMemcpyAsync(d.inst.p, inst.data(), sizeof(InstDesc) * k, cudaMemcpyHostToDevice, s));
+    APS_TRY(d.vinst.alloc((size_t)N, s));
+    APS_TRY(d.cptr.alloc((size_t)N + 1, s));
+    APS_CUDA(cudaMemcpyAsync(d.cptr.p, indptr, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToDevice, s));
+    APS_TRY(d.len.alloc((size_t)N, s));
+    APS_TRY(d.mw.alloc((size_t)N, s));
+    APS_TRY(d.split.alloc((size_t)N, s));
+    APS_TRY(d.qsplit.alloc((size_t)N, s));
+    APS_TRY(d.mwpre.alloc((size_t)N, s));
+    APS_TRY(d.crank.alloc((size_t)nnz, s));
+    APS_TRY(d.cval.alloc((size_t)nnz, s));
+    APS_TRY(d.nnz_d.alloc((size_t)M, s));
+    APS_TRY(d.mw_d.alloc((size_t)M, s));
+    APS_TRY(d.mwr.alloc((size_t)M, s));
+    APS_TRY(d.rank_of_dim.alloc((size_t)M, s));
+    APS_TRY(d.dim_of_rank.alloc((size_t)M, s));
+    APS_TRY(d.lptr.alloc((size_t)M + 1, s));
+
+    DBuf<int32_t> erow;
+    DBuf<float> vout;
+    DBuf<unsigned long long> err;
+    APS_TRY(erow.alloc((size_t)nnz, s));
+    APS_TRY(vout.alloc((size_t)nnz, s));
+    APS_TRY(err.alloc(4, s));
+    APS_CUDA(cudaMemsetAsync(err.p, 0xff, sizeof(unsigned long long), s));
+    APS_CUDA(cudaMemsetAsync(err.p + 1, 0, 3 * sizeof(unsigned long long), s));
+
+    const unsigned gN = grid_for(N, T256), gE = grid_for(nnz, T256), gM = grid_for(M, T256);
+    // ---- a1: validation, |x|, maxweight(x), per-dimension statistics
+    k_vinst<<<gN, T256, 0, s>>>(d.inst.p, k, N, d.vinst.p);
+    APS_LAUNCH_CHECK();
+    k_validate<<<gN, T256, 0, s>>>(indptr, idx, val, d.vinst.p, d.inst.p, N, nnz, ix->flags, erow.p, vout.p,
+                                   d.len.p, d.mw.p, err.p);
+    APS_LAUNCH_CHECK();
+    unsigned long long e_h = ~0ull;
+    APS_CUDA(cudaMemcpyAsync(&e_h, err.p, sizeof(e_h), cudaMemcpyDeviceToHost, s));
+    APS_CUDA(cudaStreamSynchronize(s));
+    if (e_h != ~0ull) {
+        long long row = (long long)(e_h >> 8);
+        int code = (int)(e_h & 0xff);
+        int inst_id = 0;
+        for (int i = 0; i < k; i++)
+            if (inst[i].vbase <= row) inst_id = i;
+        if (k > 1)
+            set_error("invalid input in instance %d, row %lld: %s", inst_id, row - (long long)inst[inst_id].vbase,
+                      code_name(code));
+        else
+            set_error("invalid input at row %lld: %s", row, code_name(code));
+        return APS_EINVAL;
+    }
+    APS_CUDA(cudaMemsetAsync(d.nnz_d.p, 0, sizeof(int32_t) * M, s));
+    APS_CUDA(cudaMemsetAsync(d.mw_d.p, 0, sizeof(float) * M, s));
+    if (nnz > 0) {
+        k_dimstats<<<gE, T256, 0, s>>>(idx, vout.p, erow.p, d.vinst.p, d.inst.p, nnz, d.nnz_d.p, d.mw_d.p);
+        APS_LAUNCH_CHECK();
+    }
+    // ---- a2: dimension ranks and rank-ordered rows
+    {
+        DBuf<uint64_t> keys;
+        DBuf<uint32_t> vals;
+        APS_TRY(keys.alloc((size_t)M, s));
+        APS_TRY(vals.alloc((size_t)M, s));
+        int nb = bits_for((uint64_t)maxn);
+        k_rank_keys<<<gM, T256, 0, s>>>(d.nnz_d.p, d.inst.p, k, M, nb, (uint64_t)maxn, keys.p, vals.p);
+        APS_LAUNCH_CHECK();
+        APS_TRY(sort_pairs(keys.p, vals.p, M, nb + bits_for((uint64_t)(k - 1)), s));
+        k_rank_scatter<<<gM, T256, 0, s>>>(vals.p, d.inst.p, k, M, d.mw_d.p, d.rank_of_dim.p, d.dim_of_rank.p,
+                                           d.mwr.p);
+        APS_LAUNCH_CHECK();
+    }
+    if (nnz > 0) {
+        DBuf<uint64_t> keys;
+        DBuf<uint32_t> vals;
+        APS_TRY(keys.alloc((size_t)nnz, s));
+        APS_TRY(vals.alloc((size_t)nnz, s));
+        int rb = bits_for((uint64_t)(maxm - 1));
+        if (rb == 0) rb = 1;
+        k_canon_keys<<<gE, T256, 0, s>>>(idx, erow.p, d.vinst.p, d.inst.p, d.rank_of_dim.p, nnz, rb, keys.p, vals.p);
+        APS_LAUNCH_CHECK();
+        APS_TRY(sort_pairs(keys.p, vals.p, nnz, rb + bits_for((uint64_t)(N - 1)), s));
+        k_canon_gather<<<gE, T256, 0, s>>>(keys.p, vals.p, vout.p, nnz, (1ull << rb) - 1, d.crank.p, d.cval.p);
+        APS_LAUNCH_CHECK();
+    }
+    // ---- a3: partial-indexing split
+    k_split<<<gN, T256, 0, s>>>(d.cptr.p, d.crank.p, d.cval.p, d.mwr.p, d.vinst.p, d.inst.p, N, ix->flags,
+                                d.split.p, d.qsplit.p, d.mwpre.p);
+    APS_LAUNCH_CHECK();
+    // ---- a4: suffix inverted index
+    {
+        int wb = std::max(1, bits_for((uint64_t)(maxnw - 1)));
+        DBuf<uint64_t> keys;
+        DBuf<uint32_t> vals;
+        DBuf<int32_t> lcount;
+        APS_TRY(keys.alloc((size_t)nnz, s));
+        APS_TRY(vals.alloc((size_t)nnz, s));
+        APS_TRY(lcount.alloc((size_t)M, s));
+        APS_CUDA(cudaMemsetAsync(lcount.p, 0, sizeof(int32_t) * M, s));
+        unsigned long long *nsuf_d = err.p + 1;
+        if (nnz > 0) {
+            k_post_keys<<<gE, T256, 0, s>>>(d.cptr.p, d.crank.p, erow.p, d.split.p, d.len.p, d.vinst.p, d.inst.p,
+                                            nnz, M, wb, keys.p, vals.p, nsuf_d);
+            APS_LAUNCH_CHECK();
+        }
+        unsigned long long nsuf_h = 0;
+        APS_CUDA(cudaMemcpyAsync(&nsuf_h, nsuf_d, sizeof(nsuf_h), cudaMemcpyDeviceToHost, s));
+        APS_CUDA(cudaStreamSynchronize(s));
+        ix->nsuf = (int64_t)nsuf_h;
+        if (nnz > 0) APS_TRY(sort_pairs(keys.p, vals.p, nnz, bits_for((uint64_t)M) + wb + 16, s));
+        APS_TRY(d.post.alloc((size_t)std::max<int64_t>(ix->nsuf, 1), s));
+        APS_TRY(d.wptr.alloc((size_t)std::max<int64_t>(nwptr, 1), s));
+        if (nwptr) APS_CUDA(cudaMemsetAsync(d.wptr.p, 0, sizeof(int32_t) * nwptr, s));
+        if (ix->nsuf > 0) {
+            k_post_fill<<<grid_for(ix->nsuf, T256), T256, 0, s>>>(keys.p, vals.p, erow.p, d.cval.p, d.vinst.p,
+                                                                  d.inst.p, k, ix->nsuf, wb, d.post.p, lcount.p,
+                                                                  d.wptr.p);
+            APS_LAUNCH_CHECK();
+        }
+        APS_TRY(scan_exclusive(lcount.p, d.lptr.p, M, s));
+        if (nwptr) {
+            k_wptr_scan<<<gM, T256, 0, s>>>(d.inst.p, k, M, d.wptr.p);
+            APS_LAUNCH_CHECK();
+        }
+    }
+    // ---- join work list
+    {
+        DBuf<uint64_t> keys;
+        DBuf<uint32_t> vals;
+        APS_TRY(keys.alloc((size_t)std::max<int64_t>(N, 1), s));
+        APS_TRY(vals.alloc((size_t)std::max<int64_t>(N, 1), s));
+        unsigned long long *cc = err.p;  // reuse 4 counters
+        APS_CUDA(cudaMemsetAsync(cc, 0, 4 * sizeof(unsigned long long), s));
+        if (N > 0) {
+            k_item_keys<<<gN, T256, 0, s>>>(d.cptr.p, d.crank.p, d.lptr.p, d.vinst.p, d.inst.p, N, keys.p, vals.p,
+                                            cc);
+            APS_LAUNCH_CHECK();
+            APS_TRY(sort_pairs(keys.p, vals.p, N, 35, s));
+        }
+        unsigned long long cnt_h[4] = {0, 0, 0, 0};
+        APS_CUDA(cudaMemcpyAsync(cnt_h, cc, sizeof(cnt_h), cudaMemcpyDeviceToHost, s));
+        APS_CUDA(cudaStreamSynchronize(s));
+        int64_t acc = 0;
+        for (int c = 0; c < 4; c++) {
+            ix->class_begin[c] = acc;
+            acc += (int64_t)cnt_h[c];
+        }
+        ix->class_begin[4] = acc;
+        APS_TRY(ix->items.alloc((size_t)std::max<int64_t>(acc, 1), s));
+        if (acc > 0) {
+            k_take_vals<<<grid_for(acc, T256), T256, 0, s>>>(vals.p, acc, ix->items.p);
+            APS_LAUNCH_CHECK();
+        }
+    }
+    APS_CUDA(cudaStreamSynchronize(s));
+    return APS_OK;
+}
+
+}  // namespace aps

@@ -1,0 +1,113 @@
+// Device-resident inverted index (Alg. 1's I plus the all-pairs-1/2 per-vector data).
+//
+// Layout in HBM (N vectors over all instances, M = sum of instance dimension counts):
+//   cptr[N+1]   row pointers (the caller's CSR row pointers, concatenated)
+//   crank/cval  each row's components, re-ordered by dimension rank (rank local to the
+//               instance; ranks sort dimensions by decreasing non-zero count)
+//   len, mw, split, qsplit, mwpre [N]   |x|, maxweight(x), |x'| (unindexed prefix),
+//               remscore boundary, maxweight(x')
+//   mwr/nnzr[M] maxweight_i(V) and non-zero count by global rank
+//   lptr[M+1]   posting-list start by global rank
+//   post[]      posting entries {int32 local vector id, float32 weight} (8 bytes);
+//               inside a list, entries are grouped by candidate window (ids
+//               [w*W, (w+1)*W)), and inside a window ordered by decreasing |y| (ties by
+//               id), so that minsize removes a tail of every window segment.
+//   wptr[]      window offsets inside each list, only for instances with > 1 window
+#pragma once
+
+#include "aps_internal.cuh"
+
+namespace aps {
+
+constexpr int JOIN_THREADS = 1024;
+constexpr int JOIN_WMAX = 40960;  // accumulator slots of a whole CTA (160 KB)
+constexpr int JOIN_RMAX = 4096;   // dense rank table for dot(x, y') lookups (16 KB)
+
+struct InstDesc {
+    int64_t vbase;   // first global vector id
+    int64_t qwbase;  // first (vector, window) slot of the per-window pair counts
+    int64_t wbase;   // first wptr entry (instances with nw > 1)
+    int64_t ebase;   // first component (nnz offset)
+    int32_t n;       // vectors
+    int32_t m;       // dimensions
+    int32_t rbase;   // first global rank
+    int32_t nw;      // candidate windows
+    int32_t W;       // window width
+    int32_t G;       // query groups per CTA for this instance's class
+    float t;         // threshold
+    int32_t pad;
+};
+
+struct Segment {      // one contiguous run of emitted pairs of one (x, window)
+    int64_t src;      // offset in the staging buffer
+    int64_t qw;       // (vector, window) slot: destination = scan(counts)[qw]
+    int32_t cnt;      // pairs
+    int32_t i;        // local id of x
+};
+
+struct IndexArrays {
+    DBuf<InstDesc> inst;
+    DBuf<int32_t> vinst;  // instance of each vector
+    DBuf<int64_t> cptr;
+    DBuf<int32_t> crank;
+    DBuf<float> cval;
+    DBuf<int32_t> len, split, qsplit;
+    DBuf<float> mw, mwpre;
+    DBuf<int32_t> rank_of_dim, dim_of_rank, nnz_d;
+    DBuf<float> mw_d, mwr;
+    DBuf<int64_t> lptr;
+    DBuf<int32_t> wptr;
+    DBuf<int2> post;
+};
+
+}  // namespace aps
+
+struct aps_index {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint32_t flags = 0;
+    int32_t k = 0;     // instances
+    int64_t N = 0;     // vectors
+    int64_t M = 0;     // dimensions (all instances)
+    int64_t nnz = 0;
+    int64_t nsuf = 0;  // indexed components
+    int64_t nqw = 0;   // (vector, window) slots
+    int64_t nwptr = 0;
+    int32_t maxm = 0;
+    float t = 0.f;     // single-instance threshold
+    std::vector<aps::InstDesc> inst_h;
+    aps::IndexArrays d;
+    // join work list: vectors in decreasing estimated cost, grouped by class
+    aps::DBuf<int32_t> items;
+    int64_t class_begin[5] = {0, 0, 0, 0, 0};  // classes G = 1, 2, 4, 8
+    // output sizing from the previous join
+    int64_t hint_pairs = 0;
+    int64_t hint_segs = 0;
+    aps_stats stats{};
+};
+
+namespace aps {
+
+struct PairsAlloc {          // bookkeeping behind aps_pairs._priv
+    void *block = nullptr;   // one allocation holding i, j and score
+    cudaStream_t stream = nullptr;
+    int on_device = 1;
+    int refs = 1;            // aps_pairs views sharing the block (batched results)
+};
+
+void pairs_release(aps_pairs *p);
+// Replace device pairs by one pinned host copy.
+aps_status pairs_to_host(aps_pairs *p, cudaStream_t s);
+
+// Build all index arrays for the instances whose CSRs are concatenated in (indptr, idx,
+// val) with global row pointers (indptr[0] = 0). Inputs are device pointers.
+aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_t *idx,
+                              const float *val, const std::vector<InstDesc> &inst_in,
+                              cudaStream_t s);
+
+// Self-join of every instance of the index; fills a device aps_pairs (i, j, score)
+// with per-instance ranges in pair_offsets_h (k+1 entries, may be null).
+aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out,
+                          std::vector<int64_t> *pair_offsets_h);
+
+}  // namespace aps

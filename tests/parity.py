@@ -1,0 +1,40 @@
+"""Comparison of a CUDA result with the oracle's pair set (shared by the GPU tests).
+
+Acceptance: pairs sorted by (i, j) with i < j (self-joins), identical pair sets except
+pairs whose float64 score lies within `band` of t, and float32 scores within `tol` of
+the float64 score."""
+import numpy as np
+
+
+def row_dot64(c, a, b):
+    ia, va = c.row(int(a))
+    ib, vb = c.row(int(b))
+    common, pa, pb = np.intersect1d(ia, ib, assume_unique=True, return_indices=True)
+    return float(np.dot(va[pa].astype(np.float64), vb[pb].astype(np.float64)))
+
+
+def compare(i, j, s, ref, t, n, *, band=1e-5, tol=1e-5, self_join=True, csr=None):
+    i = np.asarray(i, np.int64)
+    j = np.asarray(j, np.int64)
+    s = np.asarray(s, np.float64)
+    keys = i * n + j
+    assert np.all(np.diff(keys) > 0), "pairs must be strictly increasing in (i, j)"
+    if self_join:
+        assert np.all(i < j), "self-join pairs must have i < j"
+    rk = ref.keys(n)
+    gpu_only = np.setdiff1d(keys, rk, assume_unique=True)
+    ref_only = np.setdiff1d(rk, keys, assume_unique=True)
+    rmap = dict(zip(rk.tolist(), ref.s.tolist()))
+    for k in ref_only.tolist():
+        assert abs(rmap[k] - t) <= band, f"missing pair {divmod(k, n)} score {rmap[k]} (t={t})"
+    for k in gpu_only.tolist():
+        a, b = divmod(k, n)
+        sc = row_dot64(csr, a, b) if csr is not None else s[np.searchsorted(keys, k)]
+        assert abs(sc - t) <= band, f"extra pair {(a, b)} score {sc} (t={t})"
+    common = np.intersect1d(keys, rk, assume_unique=True)
+    gi = np.searchsorted(keys, common)
+    ri = np.searchsorted(rk, common)
+    err = np.abs(s[gi] - ref.s[ri]).max() if common.size else 0.0
+    assert err <= tol, f"score error {err} > {tol}"
+    return {"pairs": int(keys.size), "ref": int(rk.size), "max_err": float(err),
+            "gpu_only": int(gpu_only.size), "ref_only": int(ref_only.size)}

@@ -1,0 +1,339 @@
+"""GPU parity of the sparse path: every step of the index build and the self-join,
+through the C ABI, against the CPU oracle on the same seeded inputs."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def aps():
+    import torch
+
+    import paper_1402_3010_gb300 as aps
+    from paper_1402_3010_gb300 import _build
+
+    _build.build()
+    aps.load()
+    torch.cuda.init()
+    return aps
+
+
+def f32(t):
+    return float(np.float32(t))
+
+
+def run_join(aps, c, t, build_flags=0, join_flags=0, device_input=True):
+    import torch
+
+    if device_input:
+        ip, ix, vv = (torch.from_numpy(a).cuda() for a in (c.indptr, c.idx, c.val))
+    else:
+        ip, ix, vv = c.indptr, c.idx, c.val
+    h = aps.aps_build_index(ip, ix, vv, c.n, c.m, t, build_flags)
+    try:
+        p = aps.aps_all_pairs(h, join_flags)
+        try:
+            i, j, s = aps.pairs_to_numpy(p)
+        finally:
+            aps.aps_pairs_free(p)
+        st = aps.aps_index_stats(h)
+    finally:
+        aps.aps_index_free(h)
+    return i, j, s, st
+
+
+def pl_small(seed, n, m, zipf=1.0, mean_alpha=synth.ALPHA_MEAN50, hi=300, weights="lognormal"):
+    rng = np.random.default_rng(seed)
+    lengths = synth.power_law_lengths(rng, n, mean_alpha, 1, min(hi, m))
+    return synth.sparse_vectors(n, m, lengths, zipf, weights, seed, rng=rng)
+
+
+# ------------------------------------------------------------------- self-join
+
+
+def test_small_config_full_parity(aps):
+    c, t = synth.config_small()
+    i, j, s, st = run_join(aps, c, t)
+    ref = oracle.bruteforce(c, f32(t))
+    r = compare(i, j, s, ref, f32(t), c.n, csr=c)
+    assert r["pairs"] > 0
+    assert st["pairs"] == len(i)
+    assert st["evaluations"] == c.n * (c.n - 1) // 2
+    assert st["visits"] > 0 and st["candidates"] >= st["pairs"]
+
+
+@pytest.mark.parametrize("seed,t", [(11, 0.5), (12, 0.7), (13, 0.9), (14, 0.3)])
+def test_power_law_shapes_parity(aps, seed, t):
+    c = pl_small(seed, n=3000, m=2000)
+    i, j, s, _ = run_join(aps, c, t)
+    compare(i, j, s, oracle.bruteforce(c, f32(t)), f32(t), c.n, csr=c)
+
+
+@pytest.mark.parametrize("n", [5121, 10241, 20481])
+def test_every_group_class_and_ragged_sizes(aps, n):
+    """Instance sizes just past each group-class boundary (8, 4, 2 and 1 query groups
+    per CTA) with a ragged last window."""
+    c = pl_small(20 + n % 7, n=n, m=4000, hi=60)
+    t = 0.8
+    i, j, s, _ = run_join(aps, c, t)
+    ref, _ = oracle.all_pairs(c, f32(t), oracle.ALL_PAIRS_2)
+    compare(i, j, s, ref, f32(t), c.n, csr=c)
+
+
+def test_multi_window_instance(aps):
+    """n > 40960: two candidate windows per early query, ragged second window."""
+    c = pl_small(31, n=45000, m=20000, hi=40)
+    t = 0.85
+    i, j, s, st = run_join(aps, c, t)
+    ref, _ = oracle.all_pairs(c, f32(t), oracle.ALL_PAIRS_2)
+    compare(i, j, s, ref, f32(t), c.n, csr=c)
+
+
+@pytest.mark.parametrize(
+    "build_flags,join_flags",
+    [(0, 0), (8, 0), (0, 0x10), (0, 0x20), (0, 0x40), (0, 0x70), (8, 0x70), (4, 0), (2, 0)],
+)
+def test_pruning_toggles_change_work_not_results(aps, build_flags, join_flags):
+    import paper_1402_3010_gb300 as A
+
+    c = pl_small(41, n=2500, m=1500)
+    t = 0.6
+    if build_flags & A.NORMALIZE:
+        # scale rows away from unit norm; NORMALIZE must restore the same set
+        c2 = synth.SparseCSR(c.indptr, c.idx, (c.val * 3.0).astype(np.float32), c.n, c.m)
+        i, j, s, _ = run_join(aps, c2, t, build_flags, join_flags)
+    else:
+        i, j, s, _ = run_join(aps, c, t, build_flags, join_flags)
+    compare(i, j, s, oracle.bruteforce(c, f32(t)), f32(t), c.n, csr=c, tol=2e-5 if build_flags & 2 else 1e-5)
+
+
+def test_host_and_device_inputs_agree(aps):
+    c, t = synth.config_small(seed=5, n=800, m=2000)
+    a = run_join(aps, c, t, device_input=True)
+    b = run_join(aps, c, t, device_input=False)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.allclose(a[2], b[2], atol=1e-6)
+
+
+def test_host_output_flag(aps):
+    import paper_1402_3010_gb300 as A
+
+    c, t = synth.config_small(seed=6, n=700, m=1500)
+    h = A.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, t)
+    try:
+        p = A.aps_all_pairs(h, A.HOST_OUTPUT)
+        assert p.on_device == 0
+        i, j, s = A.pairs_to_numpy(p)
+        A.aps_pairs_free(p)
+    finally:
+        A.aps_index_free(h)
+    compare(i, j, s, oracle.bruteforce(c, f32(t)), f32(t), c.n, csr=c)
+
+
+def test_pair_set_is_deterministic(aps):
+    c = pl_small(51, n=4000, m=2500)
+    a = run_join(aps, c, 0.7)
+    b = run_join(aps, c, 0.7)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.abs(a[2] - b[2]).max() <= 2e-6
+
+
+# ------------------------------------------------------------------- edge cases
+
+
+def csr_raw(rows, m):
+    indptr = [0]
+    idx, val = [], []
+    for r in rows:
+        for k in sorted(r):
+            idx.append(k)
+            val.append(r[k])
+        indptr.append(len(idx))
+    return synth.SparseCSR(np.array(indptr, np.int64), np.array(idx, np.int32), np.array(val, np.float32),
+                           len(rows), m)
+
+
+@pytest.mark.parametrize(
+    "rows,m,t",
+    [
+        ([], 4, 0.5),  # empty set
+        ([{1: 1.0}], 4, 0.5),  # one vector
+        ([{}, {}, {}], 4, 0.5),  # only empty rows
+        ([{2: 1.0}] * 50 + [{3: 1.0}] * 3, 5, 1.0),  # duplicates, t = 1
+        ([{0: 1.0}, {0: 0.5, 1: 0.75}, {0: 0.5, 1: 0.25, 2: 0.75}, {1: 1.0}], 4, 0.5),  # exact ties
+        ([{0: 0.6, 1: 0.8}, {}, {0: 0.8, 1: 0.6}, {}, {1: 1.0}], 3, 0.96),
+    ],
+)
+def test_degenerate_inputs(aps, rows, m, t):
+    c = csr_raw(rows, m)
+    if c.nnz:
+        nrm = np.sqrt(np.bincount(np.repeat(np.arange(c.n), np.diff(c.indptr)),
+                                  weights=c.val.astype(np.float64) ** 2, minlength=c.n))
+        c.val = (c.val / np.repeat(np.where(nrm > 0, nrm, 1), np.diff(c.indptr))).astype(np.float32)
+    i, j, s, _ = run_join(aps, c, t, device_input=False)
+    compare(i, j, s, oracle.bruteforce(c, f32(t)), f32(t), max(c.n, 1), csr=c)
+
+
+def test_dense_dimension_in_every_vector(aps):
+    rng = np.random.default_rng(8)
+    rows = [{0: 1.0 + rng.random(), int(rng.integers(1, 300)): rng.random() + 0.1} for _ in range(3000)]
+    c = csr_raw(rows, 300)
+    nrm = np.sqrt(np.add.reduceat(c.val.astype(np.float64) ** 2, c.indptr[:-1]))
+    c.val = (c.val / np.repeat(nrm, 2)).astype(np.float32)
+    t = 0.9
+    i, j, s, _ = run_join(aps, c, t)
+    compare(i, j, s, oracle.bruteforce(c, f32(t)), f32(t), c.n, csr=c)
+
+
+# ------------------------------------------------------------------- errors
+
+
+@pytest.mark.parametrize(
+    "mutate,msg",
+    [
+        (lambda c: c.idx.__setitem__(slice(0, 2), c.idx[1::-1].copy()), "increasing"),
+        (lambda c: c.val.__setitem__(3, -c.val[3]), "value"),
+        (lambda c: c.val.__setitem__(3, np.float32(np.nan)), "value"),
+        (lambda c: c.idx.__setitem__(5, c.m + 3), "out of"),
+        (lambda c: c.val.__setitem__(slice(int(c.indptr[7]), int(c.indptr[8])), 0.9), "norm"),
+    ],
+)
+def test_malformed_input_is_rejected(aps, mutate, msg):
+    import paper_1402_3010_gb300 as A
+
+    c, t = synth.config_small(seed=9, n=100, m=400)
+    c.idx = c.idx.copy()
+    c.val = c.val.copy()
+    # make sure row 0 has two components for the ordering case
+    assert c.indptr[1] - c.indptr[0] >= 2 or msg != "increasing"
+    mutate(c)
+    with pytest.raises(A.APSError) as e:
+        A.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, t)
+    assert e.value.status == A.EINVAL
+    assert msg in str(e.value)
+
+
+@pytest.mark.parametrize("t", [0.0, -0.1, 1.5, float("nan")])
+def test_threshold_out_of_range(aps, t):
+    import paper_1402_3010_gb300 as A
+
+    c, _ = synth.config_small(seed=9, n=50, m=100)
+    with pytest.raises(A.APSError) as e:
+        A.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, t)
+    assert e.value.status == A.EINVAL
+
+
+def test_injected_allocation_failure_then_recovery(aps):
+    import paper_1402_3010_gb300 as A
+
+    c, t = synth.config_small(seed=10, n=300, m=600)
+    A.aps_debug_fail_alloc(3)
+    with pytest.raises(A.APSError) as e:
+        A.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, t)
+    assert e.value.status == A.ENOMEM
+    A.aps_debug_fail_alloc(0)
+    i, j, s, _ = run_join(aps, c, t)
+    compare(i, j, s, oracle.bruteforce(c, f32(t)), f32(t), c.n, csr=c)
+
+
+# ------------------------------------------------------------------- index steps
+
+
+def test_index_build_steps_match_oracle(aps):
+    """a1 statistics, a2 ranks and rank-ordered rows, a3 partial-indexing split and a4
+    posting lists, each against the oracle's step (bit-exact)."""
+    import paper_1402_3010_gb300 as A
+
+    c = pl_small(61, n=4000, m=3000)
+    t = 0.7
+    h = A.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, t)
+    try:
+        ex = A.aps_index_export(h)
+    finally:
+        A.aps_index_free(h)
+    ln, mw, nd, md = oracle.stats(c)
+    assert np.array_equal(ex["len"], ln)
+    assert np.array_equal(ex["mw"], mw)
+    assert np.array_equal(ex["nnz_d"], nd)
+    assert np.array_equal(ex["mw_d"], md)
+    split, mwp, aux = oracle.prefix_split(c, f32(t))
+    assert np.array_equal(ex["rank_of_dim"], aux["rank"])
+    assert np.array_equal(ex["crank"], aux["crank"])
+    assert np.array_equal(ex["cval"], aux["cval"])
+    assert np.array_equal(ex["split"], split)
+    assert np.array_equal(ex["qsplit"], split)
+    assert np.array_equal(ex["mw_pre"], mwp)
+    # posting lists: per rank, the multiset of (vector, weight) of the indexed suffixes
+    rows = np.repeat(np.arange(c.n), np.diff(c.indptr))
+    pos = np.arange(c.nnz) - c.indptr[rows]
+    suf = pos >= split[rows]
+    ref_r, ref_id, ref_w = aux["crank"][suf], rows[suf], aux["cval"][suf]
+    lp = ex["list_ptr"]
+    assert lp[-1] == suf.sum()
+    got_r = np.repeat(np.arange(c.m), np.diff(lp))
+    o1 = np.lexsort((ref_id, ref_r))
+    o2 = np.lexsort((ex["post_id"], got_r))
+    assert np.array_equal(got_r[o2], ref_r[o1])
+    assert np.array_equal(ex["post_id"][o2], ref_id[o1])
+    assert np.array_equal(ex["post_w"][o2], ref_w[o1])
+    # layout: inside a list (one candidate window here) entries by decreasing |y|, then id
+    for r in range(0, c.m, 37):
+        ids = ex["post_id"][lp[r]:lp[r + 1]]
+        key = -ln[ids].astype(np.int64) * (c.n + 1) + ids
+        assert np.all(np.diff(key) > 0)
+
+
+def test_queryable_split_uses_norm_bound(aps):
+    import paper_1402_3010_gb300 as A
+
+    c = pl_small(62, n=1500, m=1200)
+    t = 0.7
+    h = A.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, t, A.QUERYABLE)
+    try:
+        ex = A.aps_index_export(h)
+    finally:
+        A.aps_index_free(h)
+    for x in range(0, c.n, 7):
+        a, b = c.indptr[x], c.indptr[x + 1]
+        k = ex["split"][x]
+        pre = ex["cval"][a:a + k].astype(np.float64)
+        assert np.sqrt((pre ** 2).sum()) < t
+        if a + k < b:
+            nxt = ex["cval"][a:a + k + 1].astype(np.float64)
+            assert np.sqrt((nxt ** 2).sum()) * np.sqrt(1 + 2e-3) >= t * (1 - 1e-12)
+
+
+# ------------------------------------------------------------------- batched
+
+
+def test_batched_instances_match_per_instance_oracle(aps):
+    import paper_1402_3010_gb300 as A
+
+    rng = np.random.default_rng(70)
+    insts = []
+    for k in range(24):
+        n = int(np.exp(rng.uniform(np.log(5), np.log(9000))))
+        rr = np.random.default_rng([70, k])
+        lengths = synth.poisson_lengths(rr, n, 12, 1, 80)
+        c = synth.sparse_vectors(n, 3000, lengths, 1.1, "uniform", 0, rng=rr)
+        insts.append((c, f32(rng.uniform(0.6, 0.9))))
+    insts.append((csr_raw([], 5), 0.7))  # an empty instance in the middle
+    insts.append((csr_raw([{1: 1.0}], 5), 0.7))
+    args = [(c.indptr, c.idx, c.val, c.n, c.m, t) for c, t in insts]
+    outs, st = A.aps_batch_all_pairs(args)
+    try:
+        total = 0
+        for (c, t), p in zip(insts, outs):
+            i, j, s = A.pairs_to_numpy(p)
+            compare(i, j, s, oracle.bruteforce(c, t), t, max(c.n, 1), csr=c)
+            total += len(i)
+        assert st["pairs"] == total
+        assert st["evaluations"] == sum(c.n * (c.n - 1) // 2 for c, _ in insts)
+    finally:
+        for p in outs:
+            A.aps_pairs_free(p)
