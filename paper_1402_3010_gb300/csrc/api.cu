@@ -186,8 +186,9 @@ aps_status aps_index_export(const aps_index *ix, int32_t *len, float *mw, int32_
         std::vector<int2> tmp((size_t)ix->nsuf);
         APS_CUDA(cudaMemcpyAsync(tmp.data(), d.post.p, sizeof(int2) * ix->nsuf, cudaMemcpyDeviceToHost, s));
         APS_CUDA(cudaStreamSynchronize(s));
+        const int32_t mask = (ix->k == 1 && ix->inst_h[0].packed) ? 0x00ffffff : 0x7fffffff;
         for (int64_t q = 0; q < ix->nsuf; q++) {
-            if (post_id) post_id[q] = tmp[q].x;
+            if (post_id) post_id[q] = tmp[q].x & mask;
             if (post_w) memcpy(&post_w[q], &tmp[q].y, 4);
         }
     }

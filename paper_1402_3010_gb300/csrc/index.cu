@@ -3,6 +3,7 @@
 // index-insertion step of Alg. 1, done for all vectors at once).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "index.cuh"
 
@@ -153,7 +154,7 @@ __global__ void k_canon_gather(const uint64_t *__restrict__ keys, const uint32_t
 __global__ void k_split(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
                         const float *__restrict__ cval, const float *__restrict__ mwr,
                         const int32_t *__restrict__ vinst, const InstDesc *__restrict__ inst, int64_t N,
-                        uint32_t flags, int32_t *split, int32_t *qsplit, float *mwpre) {
+                        uint32_t flags, int32_t *split, int32_t *qsplit, float *mwpre, float *pnorm) {
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += (int64_t)gridDim.x * blockDim.x) {
         const InstDesc I = inst[vinst[x]];
         const double t = (double)I.t;
@@ -171,55 +172,63 @@ __global__ void k_split(const int64_t *__restrict__ cptr, const int32_t *__restr
         }
         int32_t sp = (flags & APS_NO_PARTIAL_INDEX) ? 0 : ((flags & APS_QUERYABLE) ? cs : qs);
         float best = 0.f;
-        for (int64_t p = a; p < a + sp; p++) best = fmaxf(best, cval[p]);
+        double pss = 0.0;
+        for (int64_t p = a; p < a + sp; p++) {
+            best = fmaxf(best, cval[p]);
+            pss += (double)cval[p] * (double)cval[p];
+        }
         split[x] = sp;
         qsplit[x] = qs;
         mwpre[x] = best;
+        pnorm[x] = sp ? __double2float_ru(sqrt(pss) * (1.0 + 1.1e-3)) : 0.f;
     }
 }
 
-// Suffix entries get their posting order key (global rank, window, decreasing |y|); the
-// unindexed prefix entries get a sentinel rank past the end so they sort last.
+// Suffix entries get their posting-list key (global rank); the unindexed prefix entries
+// get a sentinel past the last rank so they sort last. The sort is stable and entries
+// arrive in row order, so every list comes out in increasing vector id.
 __global__ void k_post_keys(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
                             const int32_t *__restrict__ erow, const int32_t *__restrict__ split,
-                            const int32_t *__restrict__ len, const int32_t *__restrict__ vinst,
-                            const InstDesc *__restrict__ inst, int64_t nnz, int64_t M, int wb,
-                            uint64_t *keys, uint32_t *vals, unsigned long long *nsuf) {
+                            const int32_t *__restrict__ vinst, const InstDesc *__restrict__ inst, int64_t nnz,
+                            int64_t M, uint64_t *keys, uint32_t *vals, unsigned long long *nsuf) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
         int64_t x = erow[p];
         const InstDesc &I = inst[vinst[x]];
         bool suf = (p - cptr[x]) >= split[x];
-        uint64_t key;
-        if (suf) {
-            uint64_t R = (uint64_t)I.rbase + (uint64_t)crank[p];
-            uint64_t w = (uint64_t)((x - I.vbase) / I.W);
-            uint64_t lk = 65535u - (uint64_t)min(len[x], 65535);
-            key = (R << (wb + 16)) | (w << 16) | lk;
-            atomicAdd(nsuf, 1ull);
-        } else {
-            key = (uint64_t)M << (wb + 16);
-        }
-        keys[p] = key;
+        if (suf) atomicAdd(nsuf, 1ull);
+        keys[p] = suf ? (uint64_t)I.rbase + (uint64_t)crank[p] : (uint64_t)M;
         vals[p] = (uint32_t)p;
     }
 }
 
 __global__ void k_post_fill(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
                             const int32_t *__restrict__ erow, const float *__restrict__ cval,
-                            const int32_t *__restrict__ vinst, const InstDesc *__restrict__ inst, int k,
-                            int64_t nsuf, int wb, int2 *post, int32_t *lcount, int32_t *wcount) {
+                            const int32_t *__restrict__ len, const int32_t *__restrict__ vinst,
+                            const InstDesc *__restrict__ inst, int64_t nsuf, int2 *post, int32_t *lcount,
+                            int32_t *wcount) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nsuf; q += (int64_t)gridDim.x * blockDim.x) {
         uint32_t p = vals[q];
         int64_t x = erow[p];
         const InstDesc &I = inst[vinst[x]];
-        post[q] = make_int2((int32_t)(x - I.vbase), __float_as_int(cval[p]));
-        int64_t R = (int64_t)(keys[q] >> (wb + 16));
+        const int32_t lid = (int32_t)(x - I.vbase);
+        const int32_t tag = I.packed ? (min(len[x], 255) << 24) : 0;
+        post[q] = make_int2(lid | tag, __float_as_int(cval[p]));
+        int64_t R = (int64_t)keys[q];
         atomicAdd(&lcount[R], 1);
-        if (I.nw > 1) {
-            int64_t w = (int64_t)((keys[q] >> 16) & ((1ull << wb) - 1));
-            atomicAdd(&wcount[I.wbase + (R - I.rbase) * (I.nw + 1) + w], 1);
-        }
+        if (I.nw > 1) atomicAdd(&wcount[I.wbase + (R - I.rbase) * (I.nw + 1) + lid / I.W], 1);
     }
+}
+
+// Interleaved rows and per-vector metadata read by the join.
+__global__ void k_pack(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
+                       const float *__restrict__ cval, const int32_t *__restrict__ len,
+                       const int32_t *__restrict__ split, const float *__restrict__ mwpre, int64_t N, int64_t nnz,
+                       int2 *crow, int4 *vmeta) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += stride)
+        crow[p] = make_int2(crank[p], __float_as_int(cval[p]));
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += stride)
+        vmeta[x] = make_int4((int32_t)cptr[x], len[x], split[x], __float_as_int(mwpre[x]));
 }
 
 // Window offsets inside each list of a multi-window instance: in-place exclusive scan of
@@ -296,6 +305,13 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     std::vector<InstDesc> inst = inst_in;
     int64_t N = 0, M = 0, nqw = 0, nwptr = 0;
     int32_t maxm = 1, maxn = 1, maxnw = 1;
+    // Tuning knob: APS_JOIN_MIN_GROUPS = 1, 2, 4 or 8 query groups per CTA at least
+    // (smaller candidate windows, more queries in flight per SM).
+    int gmin = 2;  // measured best on the 200k-vector workload (2 and 4 tie; 1 is 13% slower)
+    if (const char *e = getenv("APS_JOIN_MIN_GROUPS")) {
+        int v = atoi(e);
+        gmin = v >= 8 ? 8 : v >= 4 ? 4 : v >= 2 ? 2 : 1;
+    }
     for (int i = 0; i < k; i++) {
         InstDesc &I = inst[i];
         I.vbase = N;
@@ -304,7 +320,12 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
         else if (I.n <= JOIN_WMAX / 4) { I.G = 4; I.W = JOIN_WMAX / 4; }
         else if (I.n <= JOIN_WMAX / 2) { I.G = 2; I.W = JOIN_WMAX / 2; }
         else { I.G = 1; I.W = JOIN_WMAX; }
+        if (I.G < gmin) {
+            I.G = gmin;
+            I.W = JOIN_WMAX / gmin;
+        }
         I.nw = I.n > 0 ? (int32_t)((I.n + I.W - 1) / I.W) : 0;
+        I.packed = I.n < (1 << 24) ? 1 : 0;
         I.qwbase = nqw;
         I.wbase = nwptr;
         nqw += (int64_t)I.n * I.nw;
@@ -425,12 +446,12 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
         APS_LAUNCH_CHECK();
     }
     // ---- a3: partial-indexing split
+    APS_TRY(d.pnorm.alloc((size_t)std::max<int64_t>(N, 1), s));
     k_split<<<gN, T256, 0, s>>>(d.cptr.p, d.crank.p, d.cval.p, d.mwr.p, d.vinst.p, d.inst.p, N, ix->flags,
-                                d.split.p, d.qsplit.p, d.mwpre.p);
+                                d.split.p, d.qsplit.p, d.mwpre.p, d.pnorm.p);
     APS_LAUNCH_CHECK();
     // ---- a4: suffix inverted index
     {
-        int wb = std::max(1, bits_for((uint64_t)(maxnw - 1)));
         DBuf<uint64_t> keys;
         DBuf<uint32_t> vals;
         DBuf<int32_t> lcount;
@@ -440,21 +461,21 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
         APS_CUDA(cudaMemsetAsync(lcount.p, 0, sizeof(int32_t) * M, s));
         unsigned long long *nsuf_d = err.p + 1;
         if (nnz > 0) {
-            k_post_keys<<<gE, T256, 0, s>>>(d.cptr.p, d.crank.p, erow.p, d.split.p, d.len.p, d.vinst.p, d.inst.p,
-                                            nnz, M, wb, keys.p, vals.p, nsuf_d);
+            k_post_keys<<<gE, T256, 0, s>>>(d.cptr.p, d.crank.p, erow.p, d.split.p, d.vinst.p, d.inst.p, nnz, M,
+                                            keys.p, vals.p, nsuf_d);
             APS_LAUNCH_CHECK();
         }
         unsigned long long nsuf_h = 0;
         APS_CUDA(cudaMemcpyAsync(&nsuf_h, nsuf_d, sizeof(nsuf_h), cudaMemcpyDeviceToHost, s));
         APS_CUDA(cudaStreamSynchronize(s));
         ix->nsuf = (int64_t)nsuf_h;
-        if (nnz > 0) APS_TRY(sort_pairs(keys.p, vals.p, nnz, bits_for((uint64_t)M) + wb + 16, s));
+        if (nnz > 0) APS_TRY(sort_pairs(keys.p, vals.p, nnz, bits_for((uint64_t)M), s));
         APS_TRY(d.post.alloc((size_t)std::max<int64_t>(ix->nsuf, 1), s));
         APS_TRY(d.wptr.alloc((size_t)std::max<int64_t>(nwptr, 1), s));
         if (nwptr) APS_CUDA(cudaMemsetAsync(d.wptr.p, 0, sizeof(int32_t) * nwptr, s));
         if (ix->nsuf > 0) {
-            k_post_fill<<<grid_for(ix->nsuf, T256), T256, 0, s>>>(keys.p, vals.p, erow.p, d.cval.p, d.vinst.p,
-                                                                  d.inst.p, k, ix->nsuf, wb, d.post.p, lcount.p,
+            k_post_fill<<<grid_for(ix->nsuf, T256), T256, 0, s>>>(keys.p, vals.p, erow.p, d.cval.p, d.len.p,
+                                                                  d.vinst.p, d.inst.p, ix->nsuf, d.post.p, lcount.p,
                                                                   d.wptr.p);
             APS_LAUNCH_CHECK();
         }
@@ -463,6 +484,11 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
             k_wptr_scan<<<gM, T256, 0, s>>>(d.inst.p, k, M, d.wptr.p);
             APS_LAUNCH_CHECK();
         }
+        APS_TRY(d.crow.alloc((size_t)std::max<int64_t>(nnz, 1), s));
+        APS_TRY(d.vmeta.alloc((size_t)std::max<int64_t>(N, 1), s));
+        k_pack<<<grid_for(std::max(nnz, N), T256), T256, 0, s>>>(d.cptr.p, d.crank.p, d.cval.p, d.len.p, d.split.p,
+                                                                 d.mwpre.p, N, nnz, d.crow.p, d.vmeta.p);
+        APS_LAUNCH_CHECK();
     }
     // ---- join work list
     {

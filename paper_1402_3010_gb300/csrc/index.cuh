@@ -8,11 +8,16 @@
 //               remscore boundary, maxweight(x')
 //   mwr/nnzr[M] maxweight_i(V) and non-zero count by global rank
 //   lptr[M+1]   posting-list start by global rank
-//   post[]      posting entries {int32 local vector id, float32 weight} (8 bytes);
-//               inside a list, entries are grouped by candidate window (ids
-//               [w*W, (w+1)*W)), and inside a window ordered by decreasing |y| (ties by
-//               id), so that minsize removes a tail of every window segment.
-//   wptr[]      window offsets inside each list, only for instances with > 1 window
+//   crow[nnz]   the same rows interleaved as {int32 rank, float32 value} (8 bytes)
+//   vmeta[N]    {int32 row offset, int32 |x|, int32 |x'|, float32 maxweight(x')} (16 bytes)
+//   pnorm[N]    an upper bound of ||x'||_2 (with the 1e-3 norm tolerance of the queries):
+//               dot(q, x') <= ||x'||_2 for any unit q, a 4-byte first filter before vmeta
+//   post[]      posting entries {int32 local vector id | min(|y|, 255) << 24, float32
+//               weight} (8 bytes), in increasing id inside each list; the size class in
+//               the top byte lets minsize skip an entry without another load (instances
+//               with n >= 2^24 store the id only and skip no entry)
+//   wptr[]      offsets of each candidate window (ids [w*W, (w+1)*W)) inside each list,
+//               only for instances with > 1 window
 #pragma once
 
 #include "aps_internal.cuh"
@@ -21,7 +26,12 @@ namespace aps {
 
 constexpr int JOIN_THREADS = 1024;
 constexpr int JOIN_WMAX = 40960;  // accumulator slots of a whole CTA (160 KB)
-constexpr int JOIN_RMAX = 4096;   // dense rank table for dot(x, y') lookups (16 KB)
+constexpr int JOIN_RMAX = 2048;   // dense rank table for dot(x, y') lookups (8 KB)
+constexpr int JOIN_RING = 128;    // per-warp ring of candidate slots awaiting verification
+constexpr int JOIN_XCAP = 2048;   // x's row kept in shared memory when |x| <= XCAP / G
+// per-warp list of emitted pairs of one window: a warp scans at most W/NW slots rounded
+// up to 128 (W/NW = 1280 for every group shape)
+constexpr int JOIN_ECAP = JOIN_WMAX / (JOIN_THREADS / 32) + 128;
 
 struct InstDesc {
     int64_t vbase;   // first global vector id
@@ -35,7 +45,7 @@ struct InstDesc {
     int32_t W;       // window width
     int32_t G;       // query groups per CTA for this instance's class
     float t;         // threshold
-    int32_t pad;
+    int32_t packed;  // 1: posting ids carry the size class in their top byte
 };
 
 struct Segment {      // one contiguous run of emitted pairs of one (x, window)
@@ -51,8 +61,11 @@ struct IndexArrays {
     DBuf<int64_t> cptr;
     DBuf<int32_t> crank;
     DBuf<float> cval;
+    DBuf<int2> crow;
+    DBuf<int4> vmeta;
     DBuf<int32_t> len, split, qsplit;
     DBuf<float> mw, mwpre;
+    DBuf<float> pnorm;  // ||x'||_2 of the unindexed prefix (rounded up, with the norm tolerance)
     DBuf<int32_t> rank_of_dim, dim_of_rank, nnz_d;
     DBuf<float> mw_d, mwr;
     DBuf<int64_t> lptr;

@@ -9,17 +9,19 @@
 //   1. accumulate: A[y] += x[i] * y[i] over the posting lists of x's components,
 //      first over the components with remscore >= t (these may create candidates),
 //      then over the rest, which only update candidates that exist (remscore);
-//      entries with |y| below minsize are cut off (lists are ordered by |y| inside a
-//      window, so this is a tail cut found by binary search);
-//   2. verify: for every A[y] != 0, the upperbound test
+//      entries with |y| below minsize are skipped using the size class stored in the
+//      entry. Lists are in id order, so a warp's 32 lanes add into 32 increasing slots;
+//   2. verify: the non-zero slots are compacted into a per-warp ring so that every lane
+//      takes one candidate; the upperbound test
 //      A[y] + min(|y'|, |x|) * maxweight(x) * maxweight(y') >= t, then
-//      s = A[y] + dot(x, y') with y' the unindexed prefix of y;
-//      scores within a band of t are recomputed in float64 and decided there;
+//      s = A[y] + dot(x, y') with y' the unindexed prefix of y; scores within a band of
+//      t are recomputed in float64 and decided there;
 //   3. compact: warp ballots give each emitted pair its slot; one global reservation
 //      per (x, window); pairs land in a staging buffer as (y, score) in increasing y.
 // The output stage scans the per-(x, window) counts and gathers the staged runs into
 // (i, j, score) arrays, which are then in (i, j) order without a sort.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "index.cuh"
@@ -27,20 +29,19 @@
 namespace aps {
 namespace {
 
+std::atomic<int64_t> g_stage_hint{0};
+
 struct JoinParams {
     const InstDesc *inst;
     const int32_t *vinst;
     const int32_t *items;
     int64_t item_begin, item_end;
     int G;
-    const int64_t *cptr;
-    const int32_t *crank;
-    const float *cval;
-    const int32_t *len;
-    const int32_t *split;
+    const int2 *crow;    // rank-ordered rows {rank, value}
+    const int4 *vmeta;   // {row offset, |x|, |x'|, maxweight(x')}
+    const float *pnorm;  // ||y'||_2 upper bound
     const int32_t *qsplit;
     const float *mw;
-    const float *mwpre;
     const int64_t *lptr;
     const int32_t *wptr;
     const int2 *post;
@@ -54,14 +55,20 @@ struct JoinParams {
     int32_t *cntq;
     unsigned long long *counters;  // visits, candidates, verified, pairs, band
     unsigned long long *work;
+    int2 *scratch;                  // per-warp lists of emitted pairs, JOIN_ECAP each
 };
+
+constexpr int NWARPS = JOIN_THREADS / 32;
 
 __host__ __device__ constexpr int group_bytes(int G) {
     return 4 * (JOIN_WMAX / G)                       // A
-           + 8 * (JOIN_THREADS / G + 2)              // c_pref
            + 8 * (JOIN_THREADS / G)                  // c_start
+           + 4 * (JOIN_THREADS / G)                  // c_cnt
+           + 4 * (JOIN_THREADS / G + 4)              // c_ch0
            + 4 * (JOIN_THREADS / G)                  // c_xv
            + 4 * (JOIN_RMAX / G)                     // xtab
+           + 4 * JOIN_RING * (NWARPS / G)            // candidate rings
+           + 8 * (JOIN_XCAP / G)                     // x's row
            + 8 * 32                                  // wsum
            + 4 * 32                                  // wcnt
            + 8 * 4;                                  // broadcast
@@ -83,31 +90,75 @@ __device__ __forceinline__ int64_t warp_incl_scan(int64_t v, int lane) {
     return v;
 }
 
-// x's value at rank r: dense table for small ranks, binary search of x's rank-sorted row
+__device__ __forceinline__ int warp_excl_scan_int(int v, int lane, int *total) {
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    *total = __shfl_sync(0xffffffffu, inc, 31);
+    return inc - v;
+}
+
+// x's value at rank r: dense table for small ranks, binary search of x's rank-ordered row
 // otherwise.
-__device__ __forceinline__ float x_at(int r, const float *xtab, int RG, const int32_t *__restrict__ crank,
-                                      const float *__restrict__ cval, int64_t xa, int xl) {
-    if (r < RG) return xtab[r];
+__device__ __noinline__ float x_at_search(int r, const int2 *__restrict__ crow, int64_t xa, int xl) {
     int lo = 0, hi = xl;
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        if (crank[xa + mid] < r) lo = mid + 1; else hi = mid;
+        if (crow[xa + mid].x < r) lo = mid + 1; else hi = mid;
     }
-    return (lo < xl && crank[xa + lo] == r) ? cval[xa + lo] : 0.f;
+    if (lo < xl) {
+        const int2 e = crow[xa + lo];
+        if (e.x == r) return __int_as_float(e.y);
+    }
+    return 0.f;
 }
 
-// float64 dot product of two rank-sorted rows (used inside the decision band).
-__device__ double dot64(const int32_t *__restrict__ crank, const float *__restrict__ cval, int64_t xa, int xl,
-                        int64_t ya, int yl) {
+// x's value at rank r: dense table for small ranks, then a binary search of x's row held
+// in shared memory (xr, xs entries; xs = 0 when the row did not fit), else in global memory.
+__device__ __forceinline__ float x_at(int r, const float *xtab, int RG, const int2 *xr, int xs,
+                                      const int2 *__restrict__ crow, int64_t xa, int xl) {
+    if (r < RG) return xtab[r];
+    if (xs == 0) return x_at_search(r, crow, xa, xl);
+    int lo = 0, hi = xs;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (xr[mid].x < r) lo = mid + 1; else hi = mid;
+    }
+    return (lo < xs && xr[lo].x == r) ? __int_as_float(xr[lo].y) : 0.f;
+}
+
+// dot(x, y') over the |y'| leading (unindexed) entries of y's rank-ordered row.
+__device__ __forceinline__ float dot_prefix(const int2 *__restrict__ yr, int ys, const float *xtab, int RG,
+                                           const int2 *xr, int xs, const int2 *__restrict__ crow, int64_t xa,
+                                           int xl) {
+    float acc = 0.f;
+    int k = 0;
+    for (; k + 2 <= ys; k += 2) {
+        const int2 e0 = yr[k], e1 = yr[k + 1];
+        acc = fmaf(x_at(e0.x, xtab, RG, xr, xs, crow, xa, xl), __int_as_float(e0.y), acc);
+        acc = fmaf(x_at(e1.x, xtab, RG, xr, xs, crow, xa, xl), __int_as_float(e1.y), acc);
+    }
+    if (k < ys) {
+        const int2 e0 = yr[k];
+        acc = fmaf(x_at(e0.x, xtab, RG, xr, xs, crow, xa, xl), __int_as_float(e0.y), acc);
+    }
+    return acc;
+}
+
+// float64 dot product of two rank-ordered rows (used inside the decision band).
+__device__ double dot64(const int2 *__restrict__ crow, int64_t xa, int xl, int64_t ya, int yl) {
     double s = 0.0;
     int p = 0, q = 0;
     while (p < xl && q < yl) {
-        int a = crank[xa + p], b = crank[ya + q];
-        if (a == b) {
-            s += (double)cval[xa + p] * (double)cval[ya + q];
+        const int2 a = crow[xa + p], b = crow[ya + q];
+        if (a.x == b.x) {
+            s += (double)__int_as_float(a.y) * (double)__int_as_float(b.y);
             p++;
             q++;
-        } else if (a < b) {
+        } else if (a.x < b.x) {
             p++;
         } else {
             q++;
@@ -125,13 +176,18 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     const int WG = JOIN_WMAX / G, RG = JOIN_RMAX / G;
     unsigned char *base = smem + (size_t)g * group_bytes(G);
     float *A = reinterpret_cast<float *>(base);
-    int64_t *c_pref = reinterpret_cast<int64_t *>(A + WG);
-    int64_t *c_start = c_pref + GT + 2;
-    float *c_xv = reinterpret_cast<float *>(c_start + GT);
-    float *xtab = c_xv + GT;
-    int64_t *wsum = reinterpret_cast<int64_t *>(xtab + RG);
+    int64_t *c_start = reinterpret_cast<int64_t *>(A + WG);        // [GT]
+    int32_t *c_cnt = reinterpret_cast<int32_t *>(c_start + GT);    // [GT]
+    int32_t *c_ch0 = c_cnt + GT;                                    // [GT + 4] chunk prefix
+    float *c_xv = reinterpret_cast<float *>(c_ch0 + GT + 4);        // [GT]
+    float *xtab = c_xv + GT;                                        // [RG]
+    int32_t *ring = reinterpret_cast<int32_t *>(xtab + RG) + gw * JOIN_RING;
+    int2 *xr = reinterpret_cast<int2 *>(reinterpret_cast<int32_t *>(xtab + RG) + JOIN_RING * NW);
+    const int XG = JOIN_XCAP / G;
+    int64_t *wsum = reinterpret_cast<int64_t *>(xr + XG);
     int32_t *wcnt = reinterpret_cast<int32_t *>(wsum + 32);
     int64_t *bc = reinterpret_cast<int64_t *>(wcnt + 32);
+    int2 *elist = P.scratch + ((size_t)blockIdx.x * NWARPS + (threadIdx.x >> 5)) * JOIN_ECAP;
     const unsigned lt_mask = (1u << lane) - 1u;
     const bool f_minsize = !(P.flags & APS_NO_MINSIZE);
     const bool f_remscore = !(P.flags & APS_NO_REMSCORE);
@@ -139,7 +195,6 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
 
     for (int i = gt; i < WG; i += GT) A[i] = 0.f;
     unsigned long long n_visits = 0, n_cand = 0, n_verified = 0, n_band = 0, n_pairs = 0;
-    gsync(G, g, GT);
 
     for (;;) {
         gsync(G, g, GT);  // every thread is done with the previous item's broadcast slots
@@ -150,22 +205,31 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
         const int64_t x = P.items[it];
         const InstDesc I = P.inst[P.vinst[x]];
         const int32_t lx = (int32_t)(x - I.vbase);
-        const int64_t xa = P.cptr[x];
-        const int32_t xl = (int32_t)(P.cptr[x + 1] - xa);
+        const int4 xm = P.vmeta[x];
+        const int64_t xa = xm.x;
+        const int32_t xl = xm.y;
         const int32_t qs = f_remscore ? P.qsplit[x] : 0;
         const float mwx = P.mw[x];
         const float t = I.t;
         const float beta = fmaxf(1e-5f, (float)(xl + 2) * 1.1920929e-7f);  // (|x|+2) * 2^-23
         // no component reaches remscore >= t: x can create no candidate at all
         if (f_remscore ? qs >= xl : xl == 0) continue;
+        // minsize: a match y needs |y| >= t / maxweight(x) (margin for rounding and the
+        // 1e-3 norm tolerance); the size class byte of each entry is compared with it
         int smin = 0;
-        if (f_minsize && mwx > 0.f) smin = (int)ceil(((double)t - (double)beta) / ((double)mwx * 1.002));
+        if (f_minsize && I.packed && mwx > 0.f)
+            smin = min(255, (int)ceil(((double)t - (double)beta) / ((double)mwx * 1.002)));
+        const uint32_t smin_tag = (uint32_t)max(smin, 0) << 24;
+        const int32_t idmask = I.packed ? 0x00ffffff : 0x7fffffff;
+        const int ncreate = xl - qs;  // components walked first; they may create candidates
         // dense table of x over small ranks for dot(x, y')
         for (int i = gt; i < RG; i += GT) xtab[i] = 0.f;
         gsync(G, g, GT);
+        const int xs = xl <= XG ? xl : 0;  // x's row in shared memory when it fits
         for (int c = gt; c < xl; c += GT) {
-            int r = P.crank[xa + c];
-            if (r < RG) xtab[r] = P.cval[xa + c];
+            const int2 e = P.crow[xa + c];
+            if (e.x < RG) xtab[e.x] = __int_as_float(e.y);
+            if (c < xs) xr[c] = e;
         }
         gsync(G, g, GT);
 
@@ -173,97 +237,96 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
             const int w0 = w * I.W;
             const int wn = min(I.W, I.n - w0);
             const int lo = max(0, lx + 1 - w0);
-            // ---------------- accumulate: phase 0 creates candidates, phase 1 updates
-            for (int phase = 0; phase < 2; phase++) {
-                const int cb = phase == 0 ? qs : 0;
-                const int ce = phase == 0 ? xl : qs;
-                for (int c0 = cb; c0 < ce; c0 += GT) {
-                    const int c = c0 + gt;
-                    int64_t cnt = 0, st = 0;
-                    float xv = 0.f;
-                    if (c < ce) {
-                        const int r = P.crank[xa + c];
-                        const int64_t R = (int64_t)I.rbase + r;
-                        xv = P.cval[xa + c];
-                        int64_t ls = P.lptr[R], le = P.lptr[R + 1];
-                        if (I.nw > 1) {
-                            const int32_t *wp = P.wptr + I.wbase + (int64_t)r * (I.nw + 1);
-                            le = ls + wp[w + 1];
-                            ls = ls + wp[w];
-                        }
-                        if (smin > 1 && le > ls) {  // minsize: drop the tail with |y| < smin
-                            int64_t a = ls, b = le;
-                            while (a < b) {
-                                int64_t mid = (a + b) >> 1;
-                                if (P.len[I.vbase + P.post[mid].x] >= smin) a = mid + 1; else b = mid;
-                            }
-                            le = a;
-                        }
-                        cnt = le - ls;
-                        st = ls;
+            bool created = false;  // any entry of a creating component in this window
+            // ---------------- accumulate. Components are walked creating-first (those with
+            // remscore >= t), so every batch holds its creating part before its updating part.
+            for (int c0 = 0; c0 < xl; c0 += GT) {
+                const int cp = c0 + gt;
+                int64_t st = 0;
+                int32_t cnt = 0;
+                float xv = 0.f;
+                const bool ph0 = cp < ncreate;
+                if (cp < xl) {
+                    const int c = ph0 ? qs + cp : cp - ncreate;
+                    const int2 e = P.crow[xa + c];
+                    const int64_t R = (int64_t)I.rbase + e.x;
+                    xv = __int_as_float(e.y);
+                    int64_t ls = P.lptr[R], le = P.lptr[R + 1];
+                    if (I.nw > 1) {
+                        const int32_t *wp = P.wptr + I.wbase + (int64_t)e.x * (I.nw + 1);
+                        le = ls + wp[w + 1];
+                        ls = ls + wp[w];
                     }
-                    // compact the non-empty components and prefix-sum their entry counts
-                    const int64_t packed = (cnt << 11) | (cnt > 0 ? 1 : 0);
-                    const int64_t inc = warp_incl_scan(packed, lane);
-                    if (lane == 31) wsum[gw] = inc;
-                    gsync(G, g, GT);
-                    int64_t before = 0, total = 0;
-                    for (int k = 0; k < NW; k++) {
-                        int64_t s = wsum[k];
-                        if (k < gw) before += s;
-                        total += s;
-                    }
-                    const int64_t ex = before + inc - packed;
-                    if (cnt > 0) {
-                        const int pos = (int)(ex & 2047);
-                        c_pref[pos] = ex >> 11;
-                        c_start[pos] = st;
-                        c_xv[pos] = xv;
-                    }
-                    const int ncomp = (int)(total & 2047);
-                    const int64_t T = total >> 11;
-                    if (gt == 0) c_pref[ncomp] = T;
-                    gsync(G, g, GT);
-                    n_visits += (gt == 0) ? (unsigned long long)T : 0ull;
-                    // flat loop over all entries of this component batch, 128 per warp step
+                    cnt = (int32_t)(le - ls);
+                    st = ls;
+                }
+                // scan of (chunks, non-empty, non-empty creating) packed in one int64
+                const int64_t nch = (cnt + 127) >> 7;
+                const int64_t packed = (nch << 22) | ((cnt > 0 && ph0) ? (1 << 11) : 0) | (cnt > 0 ? 1 : 0);
+                const int64_t inc = warp_incl_scan(packed, lane);
+                if (lane == 31) wsum[gw] = inc;
+                gsync(G, g, GT);
+                const int64_t wv = lane < NW ? wsum[lane] : 0;
+                const int64_t winc = warp_incl_scan(wv, lane);
+                const int64_t before = __shfl_sync(0xffffffffu, winc - wv, gw);
+                const int64_t total = __shfl_sync(0xffffffffu, winc, NW - 1);
+                const int64_t ex = before + inc - packed;
+                if (cnt > 0) {
+                    const int pos = (int)(ex & 2047);
+                    c_start[pos] = st;
+                    c_cnt[pos] = cnt;
+                    c_ch0[pos] = (int32_t)(ex >> 22);
+                    c_xv[pos] = xv;
+                }
+                const int ncomp = (int)(total & 2047);
+                const int ncomp0 = (int)((total >> 11) & 2047);
+                const int nchk = (int)(total >> 22);
+                if (gt == 0) c_ch0[ncomp] = nchk;
+                gsync(G, g, GT);
+                const int P0 = c_ch0[ncomp0];
+                created = created || P0 > 0;
+                // phase 0 chunks [0, P0) create candidates; phase 1 chunks [P0, nchk) update
+                for (int phase = 0; phase < 2; phase++) {
+                    const int pb = phase == 0 ? 0 : P0, pe = phase == 0 ? P0 : nchk;
+                    if (pe <= pb) continue;
+                    if (phase == 1 && P0 > 0) gsync(G, g, GT);  // creations land before updates
+                    const int K = (pe - pb + NW - 1) / NW;
+                    int ch = pb + gw * K;
+                    const int che = min(ch + K, pe);
+                    if (ch >= che) continue;
                     int cc = 0;
-                    for (int64_t f = (int64_t)gw * 128; f < T; f += (int64_t)NW * 128) {
-                        if (c_pref[cc + 1] <= f) {  // advance to the component holding f
-                            int a = cc + 1, b = ncomp - 1;
-                            while (a < b) {
-                                int mid = (a + b) >> 1;
-                                if (c_pref[mid + 1] <= f) a = mid + 1; else b = mid;
-                            }
-                            cc = a;
+                    {  // component holding the warp's first chunk
+                        int a = 0, b = ncomp - 1;
+                        while (a < b) {
+                            const int mid = (a + b + 1) >> 1;
+                            if (c_ch0[mid] <= ch) a = mid; else b = mid - 1;
                         }
-                        const bool single = c_pref[cc + 1] >= f + 128;
+                        cc = a;
+                    }
+                    int64_t cst = c_start[cc], cen = cst + c_cnt[cc];
+                    int cch0 = c_ch0[cc];
+                    float cxv = c_xv[cc];
+                    for (; ch < che; ch++) {
+                        if (ch >= c_ch0[cc + 1]) {
+                            cc++;
+                            cst = c_start[cc];
+                            cen = cst + c_cnt[cc];
+                            cch0 = c_ch0[cc];
+                            cxv = c_xv[cc];
+                        }
+                        const int64_t e0 = cst + (int64_t)(ch - cch0) * 128 + lane;
                         int2 ent[4];
-                        float xvu[4];
-                        bool ok[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++)
+                            ent[u] = (e0 + u * 32 < cen) ? __ldg(&P.post[e0 + u * 32]) : make_int2(0, 0);
+                        if (lane == 0) n_visits += (unsigned long long)min((int64_t)128, cen - e0);
 #pragma unroll
                         for (int u = 0; u < 4; u++) {
-                            const int64_t e = f + u * 32 + lane;
-                            ok[u] = e < T;
-                            int cu = cc;
-                            if (!single) {  // each compacted component has >= 1 entry
-                                int a = cc, b = min(cc + 127, ncomp - 1);
-                                while (a < b) {
-                                    int mid = (a + b + 1) >> 1;
-                                    if (c_pref[mid] <= e) a = mid; else b = mid - 1;
-                                }
-                                cu = a;
-                            }
-                            if (ok[u]) {
-                                ent[u] = __ldg(&P.post[c_start[cu] + (e - c_pref[cu])]);
-                                xvu[u] = c_xv[cu];
-                            }
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            if (!ok[u]) continue;
-                            const int slot = ent[u].x - w0;
+                            if (e0 + u * 32 >= cen) continue;
+                            if ((uint32_t)ent[u].x < smin_tag) continue;  // minsize
+                            const int slot = (ent[u].x & idmask) - w0;
                             if (slot < lo) continue;
-                            const float prod = xvu[u] * __int_as_float(ent[u].y);
+                            const float prod = cxv * __int_as_float(ent[u].y);
                             if (phase == 0) {
                                 atomicAdd(&A[slot], prod);
                             } else if (A[slot] != 0.f) {
@@ -271,66 +334,84 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                             }
                         }
                     }
-                    gsync(G, g, GT);
                 }
-                if (!f_remscore) break;  // single phase: every component creates
+                gsync(G, g, GT);
             }
-            // ---------------- verify
-            const int span = wn - lo;
-            const int chunk = span > 0 ? (((span + NW - 1) / NW + 31) & ~31) : 0;
-            const int sb0 = lo + gw * chunk;
-            const int se = min(lo + (gw + 1) * chunk, wn);
-            int my = 0;
-            for (int sb = sb0; sb < se; sb += 32) {
-                const int s = sb + lane;
-                const bool valid = s < se;
-                const float v = valid ? A[s] : 0.f;
-                bool emit = false;
-                float sc = 0.f;
-                if (v != 0.f) {
-                    n_cand++;
-                    const int64_t gy = I.vbase + w0 + s;
-                    const int32_t ys = P.split[gy];
-                    bool ok = true;
-                    if (ys > 0) {
-                        if (f_upper) {
-                            const float bound = v + (float)min(ys, xl) * mwx * P.mwpre[gy];
-                            ok = bound >= t - beta;
-                        }
-                    } else {
-                        ok = v > t - beta;
-                    }
-                    if (ok) {
+            if (!created) continue;  // no candidate can exist in this window
+            // ---------------- verify. Slots are read 2 at a time from an even start;
+            // slots below lo or past wn are zero (never accumulated into). Candidates are
+            // compacted into a per-warp ring, verified 32 at a time, cleared from A, and
+            // the emitted (y, score) go to the warp's scratch list in increasing y.
+            const int lo2 = lo & ~1;
+            const int wn2 = (wn + 1) & ~1;
+            const int span = wn2 - lo2;
+            const int chunk = span > 0 ? (((span + NW - 1) / NW + 63) & ~63) : 0;
+            const int sb0 = lo2 + gw * chunk;
+            const int se = min(lo2 + (gw + 1) * chunk, wn2);
+            int ne = 0;
+            int head = 0, tail = 0;  // warp-uniform ring cursors
+            for (int sb = sb0; sb < se || tail > head; sb += 64) {
+                if (sb < se) {  // append this 64-slot block's candidates to the ring
+                    const int s2 = sb + lane * 2;
+                    float2 v2 = make_float2(0.f, 0.f);
+                    if (s2 < se) v2 = *reinterpret_cast<const float2 *>(&A[s2]);
+                    const int cnt = (v2.x != 0.f) + (v2.y != 0.f);
+                    int tot;
+                    int pos = tail + warp_excl_scan_int(cnt, lane, &tot);
+                    if (v2.x != 0.f) ring[(pos++) & (JOIN_RING - 1)] = s2;
+                    if (v2.y != 0.f) ring[(pos++) & (JOIN_RING - 1)] = s2 + 1;
+                    tail += tot;
+                    __syncwarp();
+                }
+                // verify full batches of 32 (and the rest once the scan is done)
+                while (tail - head >= 32 || (sb + 64 >= se && tail > head)) {
+                    const int nb = min(32, tail - head);
+                    bool emit = false;
+                    float sc = 0.f;
+                    int s = 0;
+                    if (lane < nb) {
+                        s = ring[(head + lane) & (JOIN_RING - 1)];
+                        const float v = A[s];
+                        A[s] = 0.f;
+                        const int64_t gy = I.vbase + w0 + s;
                         sc = v;
-                        const int64_t ya = P.cptr[gy];
-                        if (ys > 0) {
-                            n_verified++;
-                            float acc = 0.f;
-                            for (int k = 0; k < ys; k++) {
-                                const float xv = x_at(P.crank[ya + k], xtab, RG, P.crank, P.cval, xa, xl);
-                                acc = fmaf(xv, P.cval[ya + k], acc);
+                        // dot(x, y') <= ||y'||_2: most candidates stop here, on a 4-byte load
+                        if (v + __ldg(&P.pnorm[gy]) > t - beta) {
+                            const int4 ym = __ldg(&P.vmeta[gy]);
+                            const int ys = ym.z;
+                            bool ok = true;
+                            if (ys > 0 && f_upper)
+                                ok = v + (float)min(ys, xl) * mwx * __int_as_float(ym.w) >= t - beta;
+                            if (ok) {
+                                if (ys > 0) {
+                                    n_verified++;
+                                    sc = v + dot_prefix(P.crow + ym.x, ys, xtab, RG, xr, xs, P.crow, xa, xl);
+                                }
+                                if (sc >= t + beta) {
+                                    emit = true;
+                                } else if (sc > t - beta) {
+                                    n_band++;
+                                    const double s64 = dot64(P.crow, xa, xl, ym.x, ym.y);
+                                    emit = s64 >= (double)t;
+                                    sc = (float)s64;
+                                }
                             }
-                            sc = v + acc;
-                        }
-                        if (sc >= t + beta) {
-                            emit = true;
-                        } else if (sc > t - beta) {
-                            n_band++;
-                            const double s64 = dot64(P.crank, P.cval, xa, xl, ya, P.len[gy]);
-                            emit = s64 >= (double)t;
-                            sc = (float)s64;
                         }
                     }
-                    A[s] = emit ? sc : 0.f;
+                    const unsigned bal = __ballot_sync(0xffffffffu, emit);
+                    if (emit) elist[ne + __popc(bal & lt_mask)] = make_int2(w0 + s, __float_as_int(sc));
+                    ne += __popc(bal);
+                    n_cand += (lane < nb) ? 1ull : 0ull;
+                    head += nb;
+                    __syncwarp();  // ring slots just read may be refilled by any lane next
                 }
-                my += __popc(__ballot_sync(0xffffffffu, emit));
             }
-            if (lane == 0) wcnt[gw] = my;
+            if (lane == 0) wcnt[gw] = ne;
             gsync(G, g, GT);
             if (gt == 0) {
                 int64_t tot = 0;
                 for (int k = 0; k < NW; k++) {
-                    int c = wcnt[k];
+                    const int c = wcnt[k];
                     wcnt[k] = (int32_t)tot;
                     tot += c;
                 }
@@ -355,25 +436,12 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                 bc[2] = wr;
             }
             gsync(G, g, GT);
-            // ---------------- compact: write emitted pairs in increasing y, clear A
-            {
-                const int64_t b = bc[1];
-                const bool wr = bc[2] != 0;
-                int64_t off = b + wcnt[gw];
-                for (int sb = sb0; sb < se; sb += 32) {
-                    const int s = sb + lane;
-                    const bool valid = s < se;
-                    const float v = valid ? A[s] : 0.f;
-                    const bool emit = v != 0.f;
-                    const unsigned bal = __ballot_sync(0xffffffffu, emit);
-                    if (emit) {
-                        if (wr) P.stage[off + __popc(bal & lt_mask)] = make_int2(w0 + s, __float_as_int(v));
-                        A[s] = 0.f;
-                    }
-                    off += __popc(bal);
-                }
+            // ---------------- copy the warp's emitted pairs to the reserved run
+            if (bc[2] != 0) {
+                int2 *dst = P.stage + bc[1] + wcnt[gw];
+                for (int k = lane; k < ne; k += 32) dst[k] = elist[k];
             }
-            gsync(G, g, GT);
+            __syncwarp();
         }
     }
     // flush counters (warp-reduce, one atomic per warp)
@@ -431,11 +499,15 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     DBuf<unsigned long long> ctr;  // 0..4 counters, 5 stage count, 6 seg count, 8..11 work
     APS_TRY(cntq.alloc((size_t)std::max<int64_t>(ix->nqw, 1), s));
     APS_TRY(ctr.alloc(16, s));
-    int64_t stage_cap = std::max<int64_t>({ix->hint_pairs, (int64_t)1 << 20, ix->nnz});
-    int64_t seg_cap = std::max<int64_t>({ix->hint_segs, (int64_t)1 << 16, ix->nqw / 4});
-    if (seg_cap > ix->nqw) seg_cap = std::max<int64_t>(ix->nqw, 1);
+    // Staging capacity: the index's own hint, else the last join of this process; a join
+    // that still overflows is re-run once with the exact size. At most one segment per
+    // (vector, window) slot exists, so the segment table never overflows.
+    int64_t stage_cap = std::max<int64_t>({ix->hint_pairs, g_stage_hint.load(), (int64_t)1 << 20, ix->nnz});
+    int64_t seg_cap = std::max<int64_t>(ix->nqw, 1);
     DBuf<int2> stage;
     DBuf<Segment> segs;
+    DBuf<int2> scratch;
+    APS_TRY(scratch.alloc((size_t)sms * NWARPS * JOIN_ECAP, s));
     int64_t total_pairs = 0, total_segs = 0;
     unsigned long long ch[16];
     int reruns = 0;
@@ -455,14 +527,11 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
             P.item_begin = b;
             P.item_end = e;
             P.G = Gs[c];
-            P.cptr = d.cptr.p;
-            P.crank = d.crank.p;
-            P.cval = d.cval.p;
-            P.len = d.len.p;
-            P.split = d.split.p;
+            P.crow = d.crow.p;
+            P.vmeta = d.vmeta.p;
+            P.pnorm = d.pnorm.p;
             P.qsplit = d.qsplit.p;
             P.mw = d.mw.p;
-            P.mwpre = d.mwpre.p;
             P.lptr = d.lptr.p;
             P.wptr = d.wptr.p;
             P.post = d.post.p;
@@ -476,6 +545,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
             P.cntq = cntq.p;
             P.counters = ctr.p;
             P.work = ctr.p + 8 + c;
+            P.scratch = scratch.p;
             const int64_t nitems = e - b;
             const int64_t groups_needed = (nitems + Gs[c] - 1) / Gs[c];
             const int grid = (int)std::min<int64_t>(sms, std::max<int64_t>(groups_needed, 1));
@@ -499,6 +569,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     }
     ix->hint_pairs = total_pairs + total_pairs / 16 + 1024;
     ix->hint_segs = total_segs + total_segs / 16 + 1024;
+    g_stage_hint.store(ix->hint_pairs);
     APS_CUDA(cudaEventRecord(ev[3], s));
 
     // ---------------- output: scan counts, gather runs into (i, j, score)

@@ -17,6 +17,8 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
+import tempfile
 
 import numpy as np
 
@@ -96,6 +98,7 @@ def _distinct_zipf_rows(rng, lengths, m, s):
     if np.any(lengths > m):
         raise ValueError("row length exceeds the number of dimensions")
     cdf = bounded_zipf_cdf(m, s)
+    rbits = max(1, int(m - 1).bit_length())
     acc_row = np.zeros(0, dtype=np.int64)
     acc_rank = np.zeros(0, dtype=np.int64)
     acc_ord = np.zeros(0, dtype=np.int64)
@@ -116,17 +119,23 @@ def _distinct_zipf_rows(rng, lengths, m, s):
         all_row = np.concatenate([acc_row, rows])
         all_rank = np.concatenate([acc_rank, ranks])
         all_ord = np.concatenate([acc_ord, order])
-        key = all_row * m + all_rank
-        # first occurrence of every (row, rank) in draw order
-        srt = np.lexsort((all_ord, key))
-        key_s = key[srt]
-        first = np.ones(key_s.size, dtype=bool)
-        first[1:] = key_s[1:] != key_s[:-1]
-        keep = srt[first]
-        r_k, k_k, o_k = all_row[keep], all_rank[keep], all_ord[keep]
+        obits = max(1, int(draw_base).bit_length())
+        if all_row.size and int(all_row.max()).bit_length() + rbits + obits > 63:
+            raise ValueError("generator keys overflow int64")
+        # first occurrence of every (row, rank) in draw order: sort by (row, rank, order)
+        key = (((all_row << rbits) | all_rank) << obits) | all_ord
+        key.sort()
+        rr = key >> obits
+        first = np.ones(key.size, dtype=bool)
+        first[1:] = rr[1:] != rr[:-1]
+        key = key[first]
+        r_k = key >> (obits + rbits)
+        k_k = (key >> obits) & ((1 << rbits) - 1)
+        o_k = key & ((1 << obits) - 1)
         # keep the first lengths[r] distinct ranks of each row, by draw order
-        srt2 = np.lexsort((o_k, r_k))
-        r_k, k_k, o_k = r_k[srt2], k_k[srt2], o_k[srt2]
+        key2 = (r_k << obits) | o_k
+        srt = np.argsort(key2, kind="stable")
+        r_k, k_k, o_k = r_k[srt], k_k[srt], o_k[srt]
         starts = np.searchsorted(r_k, np.arange(n), side="left")
         pos = np.arange(r_k.size) - starts[r_k]
         sel = pos < lengths[r_k]
@@ -166,7 +175,7 @@ def sparse_vectors(
         w = rng.lognormal(0.0, 1.0, size=rows.size)
     else:
         raise ValueError(weights)
-    o = np.lexsort((ids, rows))
+    o = np.argsort((rows << 32) | ids, kind="stable")
     rows, ids, w = rows[o], ids[o], w[o]
     indptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(np.bincount(rows, minlength=n), out=indptr[1:])
@@ -193,13 +202,39 @@ ALPHA_MEAN50 = 1.4135
 ALPHA_MEAN40 = 1.4647
 
 
+CACHE_DIR = os.environ.get("APS_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "aps-synth-cache"))
+
+
+def _cached(name: str, make):
+    """Reuse a generated CSR across processes of one machine (files under CACHE_DIR)."""
+    path = os.path.join(CACHE_DIR, name + ".npz")
+    try:
+        with np.load(path) as z:
+            return SparseCSR(z["indptr"], z["idx"], z["val"], int(z["n"]), int(z["m"]))
+    except Exception:
+        pass
+    c = make()
+    try:
+        os.makedirs(CACHE_DIR, exist_ok=True)
+        tmp = path + f".{os.getpid()}.tmp.npz"
+        np.savez(tmp, indptr=c.indptr, idx=c.idx, val=c.val, n=c.n, m=c.m)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return c
+
+
 def config_large(seed: int = 2, n: int = 200_000, m: int = 100_000) -> SparseCSR:
     """Large sparse all-pairs: n=200k, m=100k, |x| power law on [1,2000] with mean ~50
     (alpha=1.4135), Zipf(1.0) ids, log-normal(0,1) weights, L2-normalised.
     Thresholds swept over {0.5, 0.7, 0.9}."""
-    rng = np.random.default_rng(seed)
-    lengths = power_law_lengths(rng, n, ALPHA_MEAN50, 1, min(2000, m))
-    return sparse_vectors(n, m, lengths, 1.0, "lognormal", seed, rng=rng)
+
+    def make():
+        rng = np.random.default_rng(seed)
+        lengths = power_law_lengths(rng, n, ALPHA_MEAN50, 1, min(2000, m))
+        return sparse_vectors(n, m, lengths, 1.0, "lognormal", seed, rng=rng)
+
+    return _cached(f"large-v2-s{seed}-n{n}-m{m}", make)
 
 
 def dense_mixture(n: int, d: int, k: int, noise_norm: float, seed: int) -> np.ndarray:
