@@ -132,6 +132,25 @@ aps_status aps_index_export(const aps_index *index, int32_t *len, float *mw, int
 aps_status aps_index_info(const aps_index *index, int32_t *n, int32_t *m, int64_t *nnz,
                           int64_t *indexed);
 
+/* Self-join of a single-instance index, as aps_all_pairs, without allocating memory.
+ * The paper has no counterpart: this exists for callers that cannot allocate device
+ * memory while they join -- a process whose memory is reserved up front by its own
+ * allocator, or a latency-critical thread that must not take the allocator's locks or
+ * trigger the implicit synchronisation an allocation can cause. The caller owns the
+ * device arrays i, j, score (capacity pairs each); on APS_OK *count pairs sorted by
+ * (i, j) are in them. All scratch comes from one fixed 64 MiB device array inside the
+ * library (held by every GPU that loads this part of the library until exit) and the
+ * join uses at most 32 CTAs. Limits: the index's (vector, window) slots must fit the
+ * arena with room left to stage pairs (else APS_EINVAL, before any work), and the pairs
+ * must fit both the staging room and `capacity` (else APS_EOVERFLOW with *count = the
+ * number of pairs). The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before any stream
+ * capture. Every call shares the one array and keeps no state in it between calls, but
+ * calls that overlap on the GPU (other streams, other host threads) race on it: run them
+ * one at a time per device. Calls no cudaMalloc/cudaFree or allocating routine. */
+aps_status aps_all_pairs_noalloc(aps_index *index, int32_t *i, int32_t *j, float *score,
+                                 int64_t capacity, int64_t *count, void *stream);
+
 /* Counters and timings of the last join on this index (see aps_stats). */
 aps_status aps_index_stats(const aps_index *index, aps_stats *out);
 

@@ -19,7 +19,7 @@ __all__ = [
     "aps_index_stats", "aps_index_free", "aps_pairs_free", "aps_pairs_copy_to",
     "aps_batch_all_pairs", "aps_all_pairs_dense", "aps_server_create", "aps_stream_submit",
     "aps_stream_poll", "aps_stream_cancel", "aps_server_free", "aps_last_error", "aps_version",
-    "aps_debug_fail_alloc", "aps_launch_count", "pairs_to_numpy", "pairs_to_torch",
+    "aps_debug_fail_alloc", "aps_launch_count", "aps_all_pairs_noalloc", "pairs_to_numpy", "pairs_to_torch",
     "DEVICE_PTRS", "NORMALIZE", "QUERYABLE", "NO_PARTIAL_INDEX", "NO_MINSIZE", "NO_REMSCORE",
     "NO_UPPERBOUND", "HOST_OUTPUT",
 ]
@@ -116,6 +116,7 @@ def load():
             "aps_version": (ctypes.c_char_p, []),
             "aps_debug_fail_alloc": (None, [_i64]),
             "aps_launch_count": (_i64, []),
+            "aps_all_pairs_noalloc": (_i32, [_P, _P, _P, _P, _i64, ctypes.POINTER(_i64), _P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -209,6 +210,23 @@ def aps_query(index: int, qptr, qidx, qval, nq: int, t: float, flags: int = 0) -
     del keep
     _check(st, "aps_query")
     return out
+
+
+def aps_all_pairs_noalloc(index: int, i, j, score, stream=None) -> int:
+    """Self-join into caller-owned CUDA int32/int32/float32 tensors of equal length (the
+    capacity), with no allocation inside the library; returns the number of pairs.
+    APSError with status EOVERFLOW carries the needed count in .count."""
+    cap = int(i.numel())
+    if int(j.numel()) != cap or int(score.numel()) != cap:
+        raise ValueError("i, j and score must have the same length")
+    cnt = _i64(0)
+    st = load().aps_all_pairs_noalloc(index, _ptr(i) if cap else None, _ptr(j) if cap else None,
+                                      _ptr(score) if cap else None, cap, ctypes.byref(cnt), _stream_ptr(stream))
+    if st != OK:
+        err = APSError(st, "aps_all_pairs_noalloc")
+        err.count = cnt.value
+        raise err
+    return cnt.value
 
 
 def aps_index_info(index: int) -> dict:

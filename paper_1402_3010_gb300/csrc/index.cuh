@@ -73,6 +73,12 @@ struct IndexArrays {
     DBuf<int2> post;
 };
 
+// The self-join of a single-instance index with every buffer carved out of `arena`
+// (arena_bytes, 256-byte aligned) and at most max_ctas CTAs; pairs land in the caller's
+// arrays (capacity cap). *count receives the number of pairs, also on APS_EOVERFLOW.
+aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes, int max_ctas, int32_t *oi,
+                        int32_t *oj, float *os, int64_t cap, int64_t *count, cudaStream_t s);
+
 }  // namespace aps
 
 struct aps_index {
@@ -122,5 +128,11 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
 // with per-instance ranges in pair_offsets_h (k+1 entries, may be null).
 aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out,
                           std::vector<int64_t> *pair_offsets_h);
+
+// The self-join of a single-instance index with every buffer carved out of `arena`
+// (arena_bytes, 256-byte aligned) and at most max_ctas CTAs; pairs land in the caller's
+// arrays (capacity cap). *count receives the number of pairs, also on APS_EOVERFLOW.
+aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes, int max_ctas, int32_t *oi,
+                        int32_t *oj, float *os, int64_t cap, int64_t *count, cudaStream_t s);
 
 }  // namespace aps

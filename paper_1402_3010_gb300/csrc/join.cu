@@ -677,4 +677,143 @@ aps_status pairs_to_host(aps_pairs *p, cudaStream_t s) {
     return APS_OK;
 }
 
+// ------------------------------------------------------------------ arena variant
+// The same join and output kernels with every buffer carved out of a caller-provided
+// device arena instead of allocated: counters, per-(x, window) counts and offsets, the
+// segment table, the per-warp emit lists (for at most max_ctas CTAs) and, in what is left,
+// the pair staging buffer. Pairs are gathered into the caller's (i, j, score) arrays.
+namespace {
+
+constexpr int SCAN1_THREADS = 1024;
+
+// Exclusive prefix sum by a single CTA, tile by tile with a running carry (no scratch).
+__global__ void __launch_bounds__(SCAN1_THREADS) k_scan_single(const int32_t *__restrict__ in, int64_t n,
+                                                               int64_t *__restrict__ out) {
+    __shared__ int64_t wt[SCAN1_THREADS / 32];
+    __shared__ int64_t carry_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += (int64_t)SCAN1_THREADS * 4) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * 4;
+        int64_t v[4], local = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            v[k] = (i0 + k < n) ? (int64_t)in[i0 + k] : 0;
+            local += v[k];
+        }
+        int64_t inc = warp_incl_scan(local, lane);
+        if (lane == 31) wt[warp] = inc;
+        __syncthreads();
+        const int64_t wv = lane < SCAN1_THREADS / 32 ? wt[lane] : 0;
+        const int64_t winc = warp_incl_scan(wv, lane);
+        const int64_t before = __shfl_sync(0xffffffffu, winc - wv, warp);
+        const int64_t tile = __shfl_sync(0xffffffffu, winc, 31);
+        int64_t run = carry_s + before + inc - local;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (i0 + k < n) out[i0 + k] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s += tile;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry_s;
+}
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes, int max_ctas, int32_t *oi,
+                        int32_t *oj, float *os, int64_t cap, int64_t *count, cudaStream_t s) {
+    IndexArrays &d = ix->d;
+    const int grid_max = std::max(1, std::min(num_sms(), max_ctas));
+    const int64_t nqw = std::max<int64_t>(ix->nqw, 1);
+    size_t off = 0;
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(arena + off);
+    off = align256(off + 16 * sizeof(unsigned long long));
+    int32_t *cntq = reinterpret_cast<int32_t *>(arena + off);
+    off = align256(off + sizeof(int32_t) * nqw);
+    int64_t *qwoff = reinterpret_cast<int64_t *>(arena + off);
+    off = align256(off + sizeof(int64_t) * (nqw + 1));
+    Segment *segs = reinterpret_cast<Segment *>(arena + off);
+    off = align256(off + sizeof(Segment) * nqw);
+    int2 *elists = reinterpret_cast<int2 *>(arena + off);
+    off = align256(off + sizeof(int2) * (size_t)grid_max * NWARPS * JOIN_ECAP);
+    if (off >= arena_bytes) {
+        set_error("index too large for the %zu-byte arena: its %lld (vector, window) slots need %zu bytes "
+                  "before any pair is staged",
+                  arena_bytes, (long long)ix->nqw, off);
+        return APS_EINVAL;
+    }
+    int2 *stage = reinterpret_cast<int2 *>(arena + off);
+    const int64_t stage_cap = (int64_t)((arena_bytes - off) / sizeof(int2));
+
+    const int Gs[4] = {1, 2, 4, 8};
+    int need = 0;
+    for (int c = 0; c < 4; c++) need = std::max(need, group_bytes(Gs[c]) * Gs[c]);
+    APS_CUDA(cudaFuncSetAttribute(join_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
+    APS_CUDA(cudaMemsetAsync(ctr, 0, 16 * sizeof(unsigned long long), s));
+    APS_CUDA(cudaMemsetAsync(cntq, 0, sizeof(int32_t) * nqw, s));
+    for (int c = 0; c < 4; c++) {
+        const int64_t b = ix->class_begin[c], e = ix->class_begin[c + 1];
+        if (e <= b) continue;
+        JoinParams P;
+        P.inst = d.inst.p;
+        P.vinst = d.vinst.p;
+        P.items = ix->items.p;
+        P.item_begin = b;
+        P.item_end = e;
+        P.G = Gs[c];
+        P.crow = d.crow.p;
+        P.vmeta = d.vmeta.p;
+        P.pnorm = d.pnorm.p;
+        P.qsplit = d.qsplit.p;
+        P.mw = d.mw.p;
+        P.lptr = d.lptr.p;
+        P.wptr = d.wptr.p;
+        P.post = d.post.p;
+        P.flags = ix->flags & (APS_NO_MINSIZE | APS_NO_REMSCORE | APS_NO_UPPERBOUND);
+        P.stage = stage;
+        P.stage_cap = stage_cap;
+        P.stage_count = ctr + 5;
+        P.segs = segs;
+        P.seg_cap = nqw;
+        P.seg_count = ctr + 6;
+        P.cntq = cntq;
+        P.counters = ctr;
+        P.work = ctr + 8 + c;
+        P.scratch = elists;
+        const int64_t groups_needed = (e - b + Gs[c] - 1) / Gs[c];
+        const int grid = (int)std::min<int64_t>(grid_max, std::max<int64_t>(groups_needed, 1));
+        join_kernel<<<grid, JOIN_THREADS, group_bytes(Gs[c]) * Gs[c], s>>>(P);
+        APS_LAUNCH_CHECK();
+    }
+    unsigned long long ch[16];
+    APS_CUDA(cudaMemcpyAsync(ch, ctr, sizeof(ch), cudaMemcpyDeviceToHost, s));
+    APS_CUDA(cudaStreamSynchronize(s));
+    const int64_t total = (int64_t)ch[5];
+    *count = total;
+    if (total > stage_cap) {
+        set_error("%lld pairs exceed the arena's staging room of %lld pairs", (long long)total, (long long)stage_cap);
+        return APS_EOVERFLOW;
+    }
+    if (total > cap) {
+        set_error("%lld pairs do not fit the caller's capacity of %lld", (long long)total, (long long)cap);
+        return APS_EOVERFLOW;
+    }
+    k_scan_single<<<1, SCAN1_THREADS, 0, s>>>(cntq, ix->nqw, qwoff);
+    APS_LAUNCH_CHECK();
+    const int64_t nseg = (int64_t)ch[6];
+    if (nseg > 0) {
+        k_gather<<<(unsigned)std::min<int64_t>(nseg, (int64_t)num_sms() * 32), 256, 0, s>>>(segs, nseg, stage, qwoff,
+                                                                                            oi, oj, os);
+        APS_LAUNCH_CHECK();
+    }
+    APS_CUDA(cudaStreamSynchronize(s));
+    return APS_OK;
+}
+
 }  // namespace aps
