@@ -383,11 +383,24 @@ aps_status aps_query(aps_index *, const int64_t *, const int32_t *, const float 
     return APS_EUNSUPPORTED;
 }
 
-aps_status aps_all_pairs_dense(const float *, int32_t, int32_t, float, uint32_t, void *, aps_pairs *out,
-                               aps_stats *) {
-    if (out) memset(out, 0, sizeof(*out));
-    set_error("aps_all_pairs_dense is not available in this build");
-    return APS_EUNSUPPORTED;
+aps_status aps_all_pairs_dense(const float *X, int32_t n, int32_t d, float t, uint32_t flags, void *stream,
+                               aps_pairs *out, aps_stats *stats) {
+    if (!out) {
+        set_error("out must not be NULL");
+        return APS_EINVAL;
+    }
+    memset(out, 0, sizeof(*out));
+    if (stats) memset(stats, 0, sizeof(*stats));
+    APS_TRY(check_threshold(t));
+    if (n < 0 || d < 64 || d > 512 || d % 64 != 0 || (n > 0 && !X)) {
+        set_error("need n >= 0, X != NULL and d a multiple of 64 in [64, 512] (got n=%d d=%d)", n, d);
+        return APS_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    aps_status st = dense_all_pairs(X, n, d, t, flags, s, out, stats);
+    if (st == APS_OK && (flags & APS_HOST_OUTPUT)) st = pairs_to_host(out, s);
+    if (st != APS_OK) pairs_release(out);
+    return st;
 }
 
 aps_status aps_server_create(aps_index *, size_t, int32_t, aps_server **out) {

@@ -1,0 +1,628 @@
+// Dense-embedding all-pairs: the matrix view S = D.D^T of the problem definition (Sec. 2.1)
+// on the 5th-generation tensor cores, then exact decisions.
+//
+//   1. X (float32) -> Xb (bfloat16, rows padded with zeros).
+//   2. dense_gemm_kernel: persistent, one CTA per SM. A CTA owns MT x 128 rows of Xb (the
+//      "A" operand, resident in shared memory) and streams 128-row blocks of Xb (the "B"
+//      operand) through a TMA ring. One thread issues tcgen05.mma (128x128x16, BF16 in,
+//      float32 accumulators in tensor memory, double-buffered); eight epilogue warps read
+//      the accumulators with tcgen05.ld and keep (i < j) with S_ij >= t - delta, where
+//      delta bounds |x.y - bf16(x).bf16(y)| plus the float32 accumulation error, so no
+//      pair with x.y >= t is lost.
+//   3. Candidates are sorted by (i, j), rescored in float32 from X (float64 when within
+//      the band of t) and compacted into the result.
+// Every wait on an mbarrier is bounded; on expiry the kernel records an error code and
+// leaves, and the host reports APS_ETIMEOUT.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "index.cuh"
+
+namespace aps {
+namespace {
+
+constexpr int DN_THREADS = 320;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-9: epilogue
+constexpr int EPI_WARPS = 8;     // two per TMEM lane quadrant, each reading half the columns
+constexpr int TILE_ROWS = 128;
+constexpr int KBLK = 64;                   // bf16 elements per 128-byte swizzle row
+constexpr int TILE_BYTES = TILE_ROWS * KBLK * 2;  // 16 KB
+constexpr int SMEM_BUDGET = 224 * 1024;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr unsigned long long WAIT_LIMIT = 1ull << 26;
+
+struct DenseParams {
+    int n, n_pad, d, KB, MT, S;
+    int nunits;
+    const int4 *units;  // {super-row block, first B block, end B block, 0}
+    float thr;
+    unsigned long long *cand;
+    unsigned long long cap;
+    unsigned long long *count;
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false (and an error code in *err) when the phase never completes or
+// another role already gave up.
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+    for (unsigned long long i = 0; i < WAIT_LIMIT; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 256) __nanosleep(64);
+        if ((i & 1023) == 1023 && *(volatile int *)err) return false;
+    }
+    atomicCAS(err, 0, code);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile of 128 rows x 128 bytes written by TMA with
+// 128-byte swizzle; 8-row core-matrix groups are 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(const void *p) {
+    const uint32_t a = smem_u32(p);
+    uint64_t d = 0;
+    d |= (uint64_t)((a & 0x3FFFF) >> 4);   // start address (16-byte units)
+    d |= (uint64_t)1 << 16;                // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;      // stride byte offset
+    d |= (uint64_t)1 << 46;                // descriptor version
+    d |= (uint64_t)2 << 61;                // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B, float32 D, both K-major, M = N = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16_128x128() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 32 consecutive columns of float32 from tensor memory (no wait).
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__global__ void __launch_bounds__(DN_THREADS, 1)
+    dense_gemm_kernel(const __grid_constant__ CUtensorMap tmap, DenseParams P) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int MT = P.MT, KB = P.KB, S = P.S;
+    unsigned char *sA = smem;
+    unsigned char *sB = smem + (size_t)MT * KB * TILE_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)S * TILE_BYTES);
+    uint64_t *a_full = bars, *a_empty = bars + 1, *done = bars + 2;
+    uint64_t *b_full = bars + 3, *b_empty = b_full + S;
+    uint64_t *d_full = b_empty + S, *d_empty = d_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d_empty + 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        mbar_init(a_full, 1);
+        mbar_init(a_empty, 1);
+        mbar_init(done, 1);
+        for (int s = 0; s < S; s++) {
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&d_full[b], 1);
+            mbar_init(&d_empty[b], EPI_WARPS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int it = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, it++) {
+                const int4 U = P.units[u];
+                if (it > 0 && !(ok = mbar_wait(a_empty, (uint32_t)(it - 1) & 1u, P.err, 1))) break;
+                mbar_expect_tx(a_full, (uint32_t)(MT * KB * TILE_BYTES));
+                for (int mt = 0; mt < MT; mt++)
+                    for (int kb = 0; kb < KB; kb++)
+                        tma_load_2d(sA + (size_t)(mt * KB + kb) * TILE_BYTES, &tmap, a_full, kb * KBLK,
+                                    (U.x * MT + mt) * TILE_ROWS);
+                for (int bc = U.y; bc < U.z && ok; bc++) {
+                    for (int kb = 0; kb < KB; kb++) {
+                        if (!(ok = mbar_wait(&b_empty[stage], phase ^ 1u, P.err, 2))) break;
+                        mbar_expect_tx(&b_full[stage], (uint32_t)TILE_BYTES);
+                        tma_load_2d(sB + (size_t)stage * TILE_BYTES, &tmap, &b_full[stage], kb * KBLK,
+                                    bc * TILE_ROWS);
+                        if (++stage == S) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_128x128();
+            int stage = 0;
+            uint32_t phase = 0;
+            int buf = 0;
+            uint32_t uses[2] = {0, 0};
+            int it = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, it++) {
+                const int4 U = P.units[u];
+                if (!(ok = mbar_wait(a_full, (uint32_t)it & 1u, P.err, 3))) break;
+                tc_fence_after();
+                for (int bc = U.y; bc < U.z && ok; bc++) {
+                    if (!(ok = mbar_wait(&d_empty[buf], (uses[buf] & 1u) ^ 1u, P.err, 4))) break;
+                    tc_fence_after();
+                    for (int kb = 0; kb < KB; kb++) {
+                        if (!(ok = mbar_wait(&b_full[stage], phase, P.err, 5))) break;
+                        tc_fence_after();
+                        const uint64_t bdesc = smem_desc(sB + (size_t)stage * TILE_BYTES);
+#pragma unroll
+                        for (int k16 = 0; k16 < KBLK / 16; k16++) {
+                            for (int mt = 0; mt < MT; mt++) {
+                                const uint64_t adesc = smem_desc(sA + (size_t)(mt * KB + kb) * TILE_BYTES);
+                                umma_bf16(tmem + (uint32_t)(buf * 256 + mt * 128), adesc + 2u * k16,
+                                          bdesc + 2u * k16, idesc, (kb | k16) != 0);
+                            }
+                        }
+                        umma_commit(&b_empty[stage]);  // the stage is free once these MMAs finish
+                        if (++stage == S) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    umma_commit(&d_full[buf]);
+                    uses[buf]++;
+                    buf ^= 1;
+                }
+                umma_commit(a_empty);
+            }
+            // every MMA issued by this thread has completed before TMEM is released
+            umma_commit(done);
+            mbar_wait(done, 0, P.err, 6);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp & 3;           // TMEM lane quadrant this warp may read
+        const int h = (warp - 2) >> 2;    // which 64-column half of each accumulator
+        int buf = 0;
+        uint32_t uses[2] = {0, 0};
+        bool ok = true;
+        for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
+            const int4 U = P.units[u];
+            for (int bc = U.y; bc < U.z; bc++) {
+                if (!(ok = mbar_wait(&d_full[buf], uses[buf] & 1u, P.err, 7))) break;
+                tc_fence_after();
+                for (int mt = 0; mt < MT; mt++) {
+                    const int i = (U.x * MT + mt) * TILE_ROWS + q * 32 + lane;
+                    const uint32_t col = (uint32_t)(buf * 256 + mt * 128 + h * 64);
+                    uint32_t r[64];
+                    tmem_ld32_issue(tmem + ((uint32_t)(q * 32) << 16) + col, r);
+                    tmem_ld32_issue(tmem + ((uint32_t)(q * 32) << 16) + col + 32, r + 32);
+                    tmem_ld_wait();
+                    float mx = __uint_as_float(r[0]);
+#pragma unroll
+                    for (int k = 1; k < 64; k++) mx = fmaxf(mx, __uint_as_float(r[k]));
+                    if (mx >= P.thr && i < P.n) {
+                        const int j0 = bc * TILE_ROWS + h * 64;
+#pragma unroll
+                        for (int k = 0; k < 64; k++) {
+                            const int j = j0 + k;
+                            if (__uint_as_float(r[k]) >= P.thr && j > i && j < P.n) {
+                                const unsigned long long pos = atomicAdd(P.count, 1ull);
+                                if (pos < P.cap)
+                                    P.cand[pos] =
+                                        (unsigned long long)i * (unsigned long long)P.n + (unsigned long long)j;
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&d_empty[buf]);
+                uses[buf]++;
+                buf ^= 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// One warp per row: float64 norm; with normalise, rows are scaled into Y; otherwise a row
+// whose norm is off by more than 1e-3 (or holds a non-finite value) is reported in *bad.
+__global__ void k_dense_rows(const float *__restrict__ X, int64_t n, int d, int normalise, float *Y,
+                             unsigned long long *bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += nw) {
+        double ss = 0.0;
+        bool finite = true;
+        for (int e = lane; e < d; e += 32) {
+            const float v = X[r * d + e];
+            finite = finite && isfinite(v);
+            ss += (double)v * (double)v;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        finite = __all_sync(0xffffffffu, finite);
+        const double nrm = sqrt(ss);
+        if (normalise) {
+            const double sc = nrm > 0.0 ? 1.0 / nrm : 0.0;
+            for (int e = lane; e < d; e += 32) Y[r * d + e] = (float)((double)X[r * d + e] * sc);
+            if (lane == 0 && (!finite || nrm == 0.0)) atomicMin(bad, (unsigned long long)r);
+        } else if (lane == 0 && (!finite || fabs(nrm - 1.0) > 1e-3)) {
+            atomicMin(bad, (unsigned long long)r);
+        }
+    }
+}
+
+__global__ void k_to_bf16(const float *__restrict__ X, int64_t n, int d, int64_t n_pad, __nv_bfloat16 *Xb) {
+    const int64_t total = n_pad * d;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        Xb[e] = (e < n * d) ? __float2bfloat16_rn(X[e]) : __float2bfloat16_rn(0.f);
+}
+
+// One warp per candidate (sorted keys i*n + j): float32 dot from X with a tree reduction;
+// float64 when the float32 score lies within the band of t.
+__global__ void k_rescore(const unsigned long long *__restrict__ keys, int64_t nc, const float *__restrict__ X, int n,
+                          int d, float t, float beta, int32_t *keep, float *score, unsigned long long *nband) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = wid; c < nc; c += nw) {
+        const unsigned long long k = keys[c];
+        const int64_t i = (int64_t)(k / (unsigned long long)n), j = (int64_t)(k % (unsigned long long)n);
+        const float *xi = X + i * d, *xj = X + j * d;
+        float acc = 0.f;
+        for (int e = lane; e < d; e += 32) acc = fmaf(xi[e], xj[e], acc);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        float s = acc;
+        bool in = s >= t;
+        if (fabsf(s - t) <= beta) {
+            double a64 = 0.0;
+            for (int e = lane; e < d; e += 32) a64 += (double)xi[e] * (double)xj[e];
+#pragma unroll
+            for (int o = 16; o; o >>= 1) a64 += __shfl_xor_sync(0xffffffffu, a64, o);
+            in = a64 >= (double)t;
+            s = (float)a64;
+            if (lane == 0) atomicAdd(nband, 1ull);
+        }
+        if (lane == 0) {
+            keep[c] = in ? 1 : 0;
+            score[c] = s;
+        }
+    }
+}
+
+__global__ void k_compact(const unsigned long long *__restrict__ keys, const int32_t *__restrict__ keep,
+                          const float *__restrict__ score, const int64_t *__restrict__ pos, int64_t nc, int n,
+                          int32_t *oi, int32_t *oj, float *os) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        if (!keep[c]) continue;
+        const int64_t p = pos[c];
+        oi[p] = (int32_t)(keys[c] / (unsigned long long)n);
+        oj[p] = (int32_t)(keys[c] % (unsigned long long)n);
+        os[p] = score[c];
+    }
+}
+
+typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                      const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                      CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                      CUtensorMapFloatOOBfill);
+
+aps_status encode_map(CUtensorMap *map, void *base, int64_t rows, int d) {
+    static PFN_encodeTiled_t fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
+            set_error("cuTensorMapEncodeTiled is not available from the driver");
+            return APS_EUNSUPPORTED;
+        }
+        fn = reinterpret_cast<PFN_encodeTiled_t>(p);
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)d * 2};
+    cuuint32_t box[2] = {(cuuint32_t)KBLK, (cuuint32_t)TILE_ROWS};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return APS_ECUDA;
+    }
+    return APS_OK;
+}
+
+std::atomic<int64_t> g_dense_hint{0};
+
+}  // namespace
+
+// Margin of the BF16 candidate test for unit vectors of dimension d: rounding both operands
+// to BF16 (unit roundoff 2^-8) changes x.y by at most (2u + u^2) ||x|| ||y||, the float32
+// accumulation adds at most 2 d 2^-23, and the 1e-3 norm tolerance scales by 1.002.
+double dense_margin(int d) {
+    const double u = std::ldexp(1.0, -8);
+    return (2.0 * u + u * u) * 1.002 + 2.0 * d * std::ldexp(1.0, -23);
+}
+
+aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t, cudaStream_t s, aps_pairs *out,
+                                  aps_stats *stats) {
+    int dev = 0, major = 0, minor = 0;
+    APS_CUDA(cudaGetDevice(&dev));
+    APS_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+    APS_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+    if (major != 10 || minor != 3) {
+        set_error("the dense path needs an sm_103 device (found sm_%d%d)", major, minor);
+        return APS_EUNSUPPORTED;
+    }
+    const int MT = d <= 256 ? 2 : 1;
+    const int KB = d / KBLK;
+    const int64_t blk = (int64_t)TILE_ROWS * MT;
+    const int64_t n_pad = std::max<int64_t>(blk, ((int64_t)n + blk - 1) / blk * blk);
+    const int abytes = MT * KB * TILE_BYTES;
+    const int S = std::min(8, (SMEM_BUDGET - abytes) / TILE_BYTES);
+    const int smem = abytes + S * TILE_BYTES + 1024 + 512;
+    cudaEvent_t ev[5];
+    for (int i = 0; i < 5; i++) APS_CUDA(cudaEventCreate(&ev[i]));
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int i = 0; i < 5; i++) cudaEventDestroy(e[i]);
+        }
+    } evg{ev};
+    APS_CUDA(cudaEventRecord(ev[0], s));
+    DBuf<__nv_bfloat16> Xb;
+    APS_TRY(Xb.alloc((size_t)(n_pad * d), s));
+    k_to_bf16<<<grid_for(n_pad * d, 256, 65536), 256, 0, s>>>(X, n, d, n_pad, Xb.p);
+    APS_LAUNCH_CHECK();
+    CUtensorMap map;
+    APS_TRY(encode_map(&map, Xb.p, n_pad, d));
+    // work units: (super-row block, run of B blocks), B blocks from the diagonal onward
+    const int64_t nsr = n_pad / blk, nb = n_pad / TILE_ROWS;
+    const int L = 32;
+    std::vector<int4> units;
+    for (int64_t sr = 0; sr < nsr; sr++)
+        for (int64_t b = sr * MT; b < nb; b += L)
+            units.push_back(make_int4((int)sr, (int)b, (int)std::min<int64_t>(b + L, nb), 0));
+    DBuf<int4> dunits;
+    APS_TRY(dunits.alloc(units.size(), s));
+    APS_CUDA(cudaMemcpyAsync(dunits.p, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, s));
+    DBuf<unsigned long long> ctr;
+    DBuf<int> err;
+    APS_TRY(ctr.alloc(4, s));
+    APS_TRY(err.alloc(1, s));
+    APS_CUDA(cudaFuncSetAttribute(dense_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const double delta = dense_margin(d);
+    int64_t cap = std::max<int64_t>({g_dense_hint.load(), (int64_t)1 << 22, (int64_t)n * 4});
+    DBuf<unsigned long long> cand;
+    int64_t nc = 0;
+    float ms_gemm = 0.f;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        APS_TRY(cand.alloc((size_t)cap, s));
+        APS_CUDA(cudaMemsetAsync(ctr.p, 0, 4 * sizeof(unsigned long long), s));
+        APS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+        DenseParams P;
+        P.n = n;
+        P.n_pad = (int)n_pad;
+        P.d = d;
+        P.KB = KB;
+        P.MT = MT;
+        P.S = S;
+        P.nunits = (int)units.size();
+        P.units = dunits.p;
+        P.thr = (float)((double)t - delta);
+        P.cand = cand.p;
+        P.cap = (unsigned long long)cap;
+        P.count = ctr.p;
+        P.err = err.p;
+        const int grid = std::max(1, std::min<int>(num_sms(), P.nunits));
+        APS_CUDA(cudaEventRecord(ev[1], s));
+        dense_gemm_kernel<<<grid, DN_THREADS, smem, s>>>(map, P);
+        APS_LAUNCH_CHECK();
+        APS_CUDA(cudaEventRecord(ev[2], s));
+        unsigned long long cnt = 0;
+        int e_h = 0;
+        APS_CUDA(cudaMemcpyAsync(&cnt, ctr.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+        APS_CUDA(cudaMemcpyAsync(&e_h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        APS_CUDA(cudaStreamSynchronize(s));
+        if (e_h) {
+            set_error("dense tensor-core kernel: a pipeline wait timed out (code %d)", e_h);
+            return APS_ETIMEOUT;
+        }
+        cudaEventElapsedTime(&ms_gemm, ev[1], ev[2]);
+        nc = (int64_t)cnt;
+        if (nc <= cap) break;
+        cap = nc + nc / 8 + 1024;
+    }
+    g_dense_hint.store(nc + nc / 8 + 1024);
+    // sort candidates by (i, j), rescore, compact
+    DBuf<uint32_t> dummy;
+    APS_TRY(dummy.alloc((size_t)std::max<int64_t>(nc, 1), s));
+    if (nc > 1) {
+        APS_CUDA(cudaMemsetAsync(dummy.p, 0, sizeof(uint32_t) * nc, s));
+        APS_TRY(sort_pairs(reinterpret_cast<uint64_t *>(cand.p), dummy.p, nc,
+                           bits_for((uint64_t)n * (uint64_t)n), s));
+    }
+    APS_CUDA(cudaEventRecord(ev[3], s));
+    DBuf<int32_t> keep;
+    DBuf<float> sc;
+    DBuf<int64_t> pos;
+    APS_TRY(keep.alloc((size_t)std::max<int64_t>(nc, 1), s));
+    APS_TRY(sc.alloc((size_t)std::max<int64_t>(nc, 1), s));
+    APS_TRY(pos.alloc((size_t)nc + 1, s));
+    const float beta = (float)std::max(1e-5, (d / 32.0 + 8.0) * std::ldexp(1.0, -23));
+    if (nc > 0) {
+        k_rescore<<<grid_for(nc * 32, 256, (int64_t)num_sms() * 64), 256, 0, s>>>(cand.p, nc, X, n, d, t, beta,
+                                                                                   keep.p, sc.p, ctr.p + 1);
+        APS_LAUNCH_CHECK();
+    }
+    APS_TRY(scan_exclusive(keep.p, pos.p, nc, s));
+    int64_t npairs = 0;
+    unsigned long long nband = 0;
+    APS_CUDA(cudaMemcpyAsync(&npairs, pos.p + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    APS_CUDA(cudaMemcpyAsync(&nband, ctr.p + 1, sizeof(nband), cudaMemcpyDeviceToHost, s));
+    APS_CUDA(cudaStreamSynchronize(s));
+    PairsAlloc *pa = new PairsAlloc();
+    pa->stream = s;
+    const size_t seg = ((size_t)npairs * 4 + 127) & ~(size_t)127;
+    aps_status st = dalloc(&pa->block, std::max<size_t>(3 * seg, 256), s);
+    if (st != APS_OK) {
+        delete pa;
+        return st;
+    }
+    char *b = static_cast<char *>(pa->block);
+    int32_t *oi = reinterpret_cast<int32_t *>(b);
+    int32_t *oj = reinterpret_cast<int32_t *>(b + seg);
+    float *os = reinterpret_cast<float *>(b + 2 * seg);
+    if (nc > 0) {
+        k_compact<<<grid_for(nc, 256, 65536), 256, 0, s>>>(cand.p, keep.p, sc.p, pos.p, nc, n, oi, oj, os);
+        APS_LAUNCH_CHECK();
+    }
+    APS_CUDA(cudaEventRecord(ev[4], s));
+    APS_CUDA(cudaEventSynchronize(ev[4]));
+    float ms_total = 0, ms_out = 0;
+    cudaEventElapsedTime(&ms_total, ev[0], ev[4]);
+    cudaEventElapsedTime(&ms_out, ev[2], ev[4]);
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->candidates = nc;
+        stats->verified = nc;
+        stats->pairs = npairs;
+        stats->band = (int64_t)nband;
+        stats->evaluations = (int64_t)n * (n - 1) / 2;
+        stats->visits = (int64_t)n * n / 2 * d;  // multiply-adds of the upper triangle
+        stats->ms_join = ms_gemm;
+        stats->ms_sort = ms_out;
+        stats->ms_total = ms_total;
+    }
+    out->count = npairs;
+    out->i = oi;
+    out->j = oj;
+    out->score = os;
+    out->on_device = 1;
+    out->_reserved = 0;
+    out->_priv = pa;
+    return APS_OK;
+}
+
+// Validate (or normalise) the rows of X and run the dense join.
+aps_status dense_all_pairs(const float *X, int32_t n, int32_t d, float t, uint32_t flags, cudaStream_t s,
+                           aps_pairs *out, aps_stats *stats) {
+    DBuf<float> dx, dy;
+    const float *Xd = X;
+    if (!(flags & APS_DEVICE_PTRS)) {
+        APS_TRY(dx.alloc((size_t)n * d, s));
+        if ((int64_t)n * d) APS_CUDA(cudaMemcpyAsync(dx.p, X, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, s));
+        Xd = dx.p;
+    }
+    DBuf<unsigned long long> bad;
+    APS_TRY(bad.alloc(1, s));
+    APS_CUDA(cudaMemsetAsync(bad.p, 0xff, sizeof(unsigned long long), s));
+    const bool norm = (flags & APS_NORMALIZE) != 0;
+    if (norm) APS_TRY(dy.alloc((size_t)n * d, s));
+    if (n > 0) {
+        k_dense_rows<<<grid_for((int64_t)n * 32, 256, 65536), 256, 0, s>>>(Xd, n, d, norm ? 1 : 0, dy.p, bad.p);
+        APS_LAUNCH_CHECK();
+    }
+    unsigned long long b = 0;
+    APS_CUDA(cudaMemcpyAsync(&b, bad.p, sizeof(b), cudaMemcpyDeviceToHost, s));
+    APS_CUDA(cudaStreamSynchronize(s));
+    if (b != ~0ull) {
+        set_error(norm ? "row %llu is zero or holds a non-finite value"
+                       : "row %llu: L2 norm differs from 1 by more than 1e-3 or a value is not finite "
+                         "(pass APS_NORMALIZE)",
+                  b);
+        return APS_EINVAL;
+    }
+    return dense_all_pairs_device(norm ? dy.p : Xd, n, d, t, s, out, stats);
+}
+
+}  // namespace aps

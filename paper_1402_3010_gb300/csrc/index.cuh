@@ -79,6 +79,14 @@ struct IndexArrays {
 aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes, int max_ctas, int32_t *oi,
                         int32_t *oj, float *os, int64_t cap, int64_t *count, cudaStream_t s);
 
+// Dense all-pairs of X[n, d] (float32 rows; host or device per APS_DEVICE_PTRS) on the
+// tensor cores with exact rescoring; d % 64 == 0, 64 <= d <= 512.
+aps_status dense_all_pairs(const float *X, int32_t n, int32_t d, float t, uint32_t flags, cudaStream_t s,
+                           aps_pairs *out, aps_stats *stats);
+aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t, cudaStream_t s, aps_pairs *out,
+                                  aps_stats *stats);
+double dense_margin(int d);
+
 }  // namespace aps
 
 struct aps_index {
@@ -134,5 +142,13 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out,
 // arrays (capacity cap). *count receives the number of pairs, also on APS_EOVERFLOW.
 aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes, int max_ctas, int32_t *oi,
                         int32_t *oj, float *os, int64_t cap, int64_t *count, cudaStream_t s);
+
+// Dense all-pairs of X[n, d] (float32 rows; host or device per APS_DEVICE_PTRS) on the
+// tensor cores with exact rescoring; d % 64 == 0, 64 <= d <= 512.
+aps_status dense_all_pairs(const float *X, int32_t n, int32_t d, float t, uint32_t flags, cudaStream_t s,
+                           aps_pairs *out, aps_stats *stats);
+aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t, cudaStream_t s, aps_pairs *out,
+                                  aps_stats *stats);
+double dense_margin(int d);
 
 }  // namespace aps

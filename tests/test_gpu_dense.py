@@ -1,0 +1,121 @@
+"""GPU parity of the dense path (BF16 tensor-core candidates + exact rescoring) against the
+float64 oracle (NumPy X @ X.T + threshold)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def aps():
+    import torch
+
+    import paper_1402_3010_gb300 as aps
+    from paper_1402_3010_gb300 import _build
+
+    _build.build()
+    aps.load()
+    torch.cuda.init()
+    return aps
+
+
+def f32(t):
+    return float(np.float32(t))
+
+
+def run_dense(aps, X, t, flags=0, device=True):
+    import torch
+
+    Xin = torch.from_numpy(np.ascontiguousarray(X)).cuda() if device else np.ascontiguousarray(X)
+    p, st = aps.aps_all_pairs_dense(Xin, t, flags)
+    try:
+        i, j, s = aps.pairs_to_numpy(p)
+    finally:
+        aps.aps_pairs_free(p)
+    return i, j, s, st
+
+
+@pytest.mark.parametrize("n,d,k", [(700, 128, 20), (3001, 256, 60), (1500, 64, 30), (1200, 512, 25), (129, 192, 5)])
+def test_dense_mixture_full_parity(aps, n, d, k):
+    X = synth.dense_mixture(n, d, k, 0.15, seed=n + d)
+    t = 0.8
+    i, j, s, st = run_dense(aps, X, t)
+    ref = oracle.dense_all_pairs(X, f32(t))
+    r = compare(i, j, s, ref, f32(t), n)
+    assert r["pairs"] > 0
+    assert st["pairs"] == len(i) and st["candidates"] >= st["pairs"]
+
+
+def test_dense_many_pairs_near_the_threshold(aps):
+    """Random directions in 64-d with t = 0.3: many scores within the BF16 margin of t, so
+    the margin and the float32/float64 decisions are exercised."""
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((2500, 64))
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    X = X.astype(np.float32)
+    t = 0.3
+    i, j, s, st = run_dense(aps, X, t)
+    ref = oracle.dense_all_pairs(X, f32(t))
+    compare(i, j, s, ref, f32(t), X.shape[0])
+    # some reference scores lie just above t: any miss there would fail compare()
+    assert np.sum((ref.s >= t) & (ref.s < t + 0.004)) > 10
+
+
+def test_dense_host_input_and_normalize(aps):
+    import paper_1402_3010_gb300 as A
+
+    X = synth.dense_mixture(900, 128, 15, 0.15, seed=9)
+    t = 0.85
+    ref = oracle.dense_all_pairs(X, f32(t))
+    a = run_dense(aps, X, t, device=False)
+    compare(a[0], a[1], a[2], ref, f32(t), 900)
+    b = run_dense(aps, (X * 2.5).astype(np.float32), t, flags=A.NORMALIZE)
+    compare(b[0], b[1], b[2], ref, f32(t), 900, tol=2e-5)
+    with pytest.raises(A.APSError) as e:
+        run_dense(aps, (X * 2.5).astype(np.float32), t)
+    assert e.value.status == A.EINVAL
+
+
+@pytest.mark.parametrize("n", [0, 1, 2])
+def test_dense_degenerate_sizes(aps, n):
+    X = synth.dense_mixture(max(n, 1), 64, 1, 0.0, seed=3)[:n]
+    i, j, s, _ = run_dense(aps, X, 0.5)
+    assert len(i) == (1 if n == 2 else 0)
+
+
+def test_dense_bad_arguments(aps):
+    import paper_1402_3010_gb300 as A
+
+    X = np.ones((4, 100), np.float32) / 10.0
+    with pytest.raises(A.APSError) as e:
+        run_dense(aps, X, 0.5)
+    assert e.value.status == A.EINVAL
+
+
+def test_dense_full_size_sampled_rows(aps):
+    """The 200k x 256 mixture in the configuration the bench times: rows sampled and
+    checked against the float64 oracle one by one."""
+    X, t = synth.config_dense()
+    i, j, s, st = run_dense(aps, X, t)
+    assert st["pairs"] == len(i) > 1_000_000
+    keys = i.astype(np.int64) * X.shape[0] + j
+    assert np.all(np.diff(keys) > 0) and np.all(i < j)
+    rows = np.random.default_rng(1).choice(X.shape[0], 40, replace=False)
+    ref = oracle.dense_rows(X, f32(t), rows)
+    sel = np.isin(i, rows) | np.isin(j, rows)
+    gk = np.unique(keys[sel])
+    rk = np.unique(ref.keys(X.shape[0]))
+    # outside the 1e-5 band the sets agree
+    rmap = dict(zip(ref.keys(X.shape[0]).tolist(), ref.s.tolist()))
+    for k in np.setdiff1d(rk, gk).tolist():
+        assert abs(rmap[k] - t) <= 1e-5
+    smap = dict(zip(keys[sel].tolist(), s[sel].tolist()))
+    for k in np.setdiff1d(gk, rk).tolist():
+        assert abs(smap[k] - t) <= 1e-5
+    common = np.intersect1d(gk, rk)
+    err = max(abs(smap[k] - rmap[k]) for k in common.tolist())
+    assert err <= 1e-5
