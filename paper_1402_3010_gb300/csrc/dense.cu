@@ -81,8 +81,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
     for (unsigned long long i = 0; i < WAIT_LIMIT; i++) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (i > 256) __nanosleep(64);
-        if ((i & 1023) == 1023 && *(volatile int *)err) return false;
+        if ((i & 4095) == 4095) {
+            if (*(volatile int *)err) return false;
+            __nanosleep(256);
+        }
     }
     atomicCAS(err, 0, code);
     return false;
@@ -145,6 +147,19 @@ __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t *r) {
 }
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Rare path: record (i, j0 + k) for every set bit k with j > i and j < n.
+__device__ __noinline__ void emit_candidates(unsigned long long mask, int i, int j0, const DenseParams &P) {
+    while (mask) {
+        const int k = __ffsll((long long)mask) - 1;
+        mask &= mask - 1ull;
+        const int j = j0 + k;
+        if (j > i && j < P.n) {
+            const unsigned long long pos = atomicAdd(P.count, 1ull);
+            if (pos < P.cap) P.cand[pos] = (unsigned long long)i * (unsigned long long)P.n + (unsigned long long)j;
+        }
+    }
+}
 
 __global__ void __launch_bounds__(DN_THREADS, 1)
     dense_gemm_kernel(const __grid_constant__ CUtensorMap tmap, DenseParams P) {
@@ -218,6 +233,8 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_128x128();
+            // descriptors of the first A tile and the first B stage; tiles are 16 KB apart
+            const uint64_t adesc0 = smem_desc(sA), bdesc0 = smem_desc(sB);
             int stage = 0;
             uint32_t phase = 0;
             int buf = 0;
@@ -234,14 +251,15 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
                     for (int kb = 0; kb < KB; kb++) {
                         if (!(ok = mbar_wait(&b_full[stage], phase, P.err, 5))) break;
                         tc_fence_after();
-                        const uint64_t bdesc = smem_desc(sB + (size_t)stage * TILE_BYTES);
+                        const uint64_t bdesc = bdesc0 + (uint64_t)(stage * (TILE_BYTES >> 4));
+                        const uint64_t adesc = adesc0 + (uint64_t)(kb * (TILE_BYTES >> 4));
+                        const uint32_t td = tmem + (uint32_t)(buf * 256);
 #pragma unroll
                         for (int k16 = 0; k16 < KBLK / 16; k16++) {
-                            for (int mt = 0; mt < MT; mt++) {
-                                const uint64_t adesc = smem_desc(sA + (size_t)(mt * KB + kb) * TILE_BYTES);
-                                umma_bf16(tmem + (uint32_t)(buf * 256 + mt * 128), adesc + 2u * k16,
+                            umma_bf16(td, adesc + 2u * k16, bdesc + 2u * k16, idesc, (kb | k16) != 0);
+                            if (MT == 2)
+                                umma_bf16(td + 128u, adesc + (uint64_t)(KB * (TILE_BYTES >> 4)) + 2u * k16,
                                           bdesc + 2u * k16, idesc, (kb | k16) != 0);
-                            }
                         }
                         umma_commit(&b_empty[stage]);  // the stage is free once these MMAs finish
                         if (++stage == S) {
@@ -279,22 +297,15 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
                     tmem_ld32_issue(tmem + ((uint32_t)(q * 32) << 16) + col, r);
                     tmem_ld32_issue(tmem + ((uint32_t)(q * 32) << 16) + col + 32, r + 32);
                     tmem_ld_wait();
-                    float mx = __uint_as_float(r[0]);
+                    // bit k: column k of this half reaches the candidate threshold
+                    uint32_t lo = 0, hi = 0;
 #pragma unroll
-                    for (int k = 1; k < 64; k++) mx = fmaxf(mx, __uint_as_float(r[k]));
-                    if (mx >= P.thr && i < P.n) {
-                        const int j0 = bc * TILE_ROWS + h * 64;
-#pragma unroll
-                        for (int k = 0; k < 64; k++) {
-                            const int j = j0 + k;
-                            if (__uint_as_float(r[k]) >= P.thr && j > i && j < P.n) {
-                                const unsigned long long pos = atomicAdd(P.count, 1ull);
-                                if (pos < P.cap)
-                                    P.cand[pos] =
-                                        (unsigned long long)i * (unsigned long long)P.n + (unsigned long long)j;
-                            }
-                        }
+                    for (int k = 0; k < 32; k++) {
+                        lo |= (__uint_as_float(r[k]) >= P.thr ? 1u : 0u) << k;
+                        hi |= (__uint_as_float(r[k + 32]) >= P.thr ? 1u : 0u) << k;
                     }
+                    unsigned long long mask = ((unsigned long long)hi << 32) | lo;
+                    if (mask != 0ull && i < P.n) emit_candidates(mask, i, bc * TILE_ROWS + h * 64, P);
                 }
                 tc_fence_before();
                 __syncwarp();
