@@ -376,13 +376,6 @@ aps_status aps_batch_all_pairs(int32_t k, const aps_instance *inst, uint32_t fla
     return st;
 }
 
-aps_status aps_query(aps_index *, const int64_t *, const int32_t *, const float *, int32_t, float, uint32_t,
-                     aps_pairs *out) {
-    if (out) memset(out, 0, sizeof(*out));
-    set_error("aps_query is not available in this build");
-    return APS_EUNSUPPORTED;
-}
-
 aps_status aps_all_pairs_dense(const float *X, int32_t n, int32_t d, float t, uint32_t flags, void *stream,
                                aps_pairs *out, aps_stats *stats) {
     if (!out) {
@@ -402,25 +395,6 @@ aps_status aps_all_pairs_dense(const float *X, int32_t n, int32_t d, float t, ui
     if (st != APS_OK) pairs_release(out);
     return st;
 }
-
-aps_status aps_server_create(aps_index *, size_t, int32_t, aps_server **out) {
-    if (out) *out = nullptr;
-    set_error("serving is not available in this build");
-    return APS_EUNSUPPORTED;
-}
-aps_status aps_stream_submit(aps_server *, const aps_query_req *, uint64_t *) {
-    set_error("serving is not available in this build");
-    return APS_EUNSUPPORTED;
-}
-aps_status aps_stream_poll(aps_server *, uint64_t, int32_t, aps_pairs *) {
-    set_error("serving is not available in this build");
-    return APS_EUNSUPPORTED;
-}
-aps_status aps_stream_cancel(aps_server *, uint64_t) {
-    set_error("serving is not available in this build");
-    return APS_EUNSUPPORTED;
-}
-void aps_server_free(aps_server *) {}
 
 const char *aps_version(void) { return "aps 0.1 (sm_103a)"; }
 

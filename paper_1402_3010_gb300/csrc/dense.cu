@@ -478,7 +478,7 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
     APS_TRY(encode_map(&map, Xb.p, n_pad, d));
     // work units: (super-row block, run of B blocks), B blocks from the diagonal onward
     const int64_t nsr = n_pad / blk, nb = n_pad / TILE_ROWS;
-    const int L = 32;
+    const int L = 64;
     std::vector<int4> units;
     for (int64_t sr = 0; sr < nsr; sr++)
         for (int64_t b = sr * MT; b < nb; b += L)

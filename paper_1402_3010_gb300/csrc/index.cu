@@ -523,4 +523,109 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     return APS_OK;
 }
 
+// ------------------------------------------------------------------ external queries
+namespace {
+
+__global__ void k_q_keys(const int32_t *__restrict__ qidx, const int32_t *__restrict__ erow,
+                         const int32_t *__restrict__ rank_of_dim, int64_t nnz, int rb, uint64_t *keys, uint32_t *vals) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        keys[p] = ((uint64_t)erow[p] << rb) | (uint64_t)rank_of_dim[qidx[p]];
+        vals[p] = (uint32_t)p;
+    }
+}
+
+__global__ void k_q_gather(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                           const float *__restrict__ vout, int64_t nnz, uint64_t rmask, int2 *crow) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x)
+        crow[q] = make_int2((int32_t)(keys[q] & rmask), __float_as_int(vout[vals[q]]));
+}
+
+// Remscore boundary of a query: the first rank-ordered component where
+// sum x[i] * maxweight_i(V) reaches t (float64, as for indexed vectors).
+__global__ void k_q_split(const int64_t *__restrict__ qptr, const int2 *__restrict__ crow,
+                          const float *__restrict__ mwr, int64_t nq, float t, int32_t *qsplit, int4 *vmeta) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nq; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = qptr[x], b = qptr[x + 1];
+        const int32_t L = (int32_t)(b - a);
+        int32_t qs = L;
+        double bmw = 0.0;
+        for (int64_t p = a; p < b; p++) {
+            bmw += (double)__int_as_float(crow[p].y) * (double)mwr[crow[p].x];
+            if (bmw >= (double)t) {
+                qs = (int32_t)(p - a);
+                break;
+            }
+        }
+        qsplit[x] = qs;
+        vmeta[x] = make_int4((int32_t)a, L, 0, 0);
+    }
+}
+
+}  // namespace
+
+aps_status prepare_queries(const aps_index *ix, const int64_t *qptr, const int32_t *qidx, const float *qval,
+                           int32_t nq, float t, uint32_t flags, cudaStream_t s, QueryArrays &qa) {
+    const IndexArrays &d = ix->d;
+    int64_t nnz = 0, first = 0;
+    APS_CUDA(cudaMemcpyAsync(&nnz, qptr + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    APS_CUDA(cudaMemcpyAsync(&first, qptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    APS_CUDA(cudaStreamSynchronize(s));
+    if (first != 0 || nnz < 0 || nnz >= (1ll << 31)) {
+        set_error("query indptr[0] must be 0 and nnz in [0, 2^31)");
+        return APS_EINVAL;
+    }
+    qa.nq = nq;
+    qa.nnz = nnz;
+    // the index's single instance describes the dimension space
+    InstDesc qd = ix->inst_h[0];
+    qd.vbase = 0;
+    qd.n = nq;
+    DBuf<InstDesc> dinst;
+    DBuf<int32_t> vinst, erow, len;
+    DBuf<float> vout;
+    DBuf<unsigned long long> err;
+    APS_TRY(dinst.alloc(1, s));
+    APS_CUDA(cudaMemcpyAsync(dinst.p, &qd, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
+    APS_TRY(vinst.alloc((size_t)std::max<int64_t>(nq, 1), s));
+    APS_CUDA(cudaMemsetAsync(vinst.p, 0, sizeof(int32_t) * std::max<int64_t>(nq, 1), s));
+    APS_TRY(erow.alloc((size_t)std::max<int64_t>(nnz, 1), s));
+    APS_TRY(vout.alloc((size_t)std::max<int64_t>(nnz, 1), s));
+    APS_TRY(len.alloc((size_t)std::max<int64_t>(nq, 1), s));
+    APS_TRY(qa.mw.alloc((size_t)std::max<int64_t>(nq, 1), s));
+    APS_TRY(err.alloc(1, s));
+    APS_CUDA(cudaMemsetAsync(err.p, 0xff, sizeof(unsigned long long), s));
+    if (nq > 0) {
+        k_validate<<<grid_for(nq, T256), T256, 0, s>>>(qptr, qidx, qval, vinst.p, dinst.p, nq, nnz, flags, erow.p,
+                                                       vout.p, len.p, qa.mw.p, err.p);
+        APS_LAUNCH_CHECK();
+    }
+    unsigned long long e_h = ~0ull;
+    APS_CUDA(cudaMemcpyAsync(&e_h, err.p, sizeof(e_h), cudaMemcpyDeviceToHost, s));
+    APS_CUDA(cudaStreamSynchronize(s));
+    if (e_h != ~0ull) {
+        set_error("invalid query row %lld: %s", (long long)(e_h >> 8), code_name((int)(e_h & 0xff)));
+        return APS_EINVAL;
+    }
+    APS_TRY(qa.crow.alloc((size_t)std::max<int64_t>(nnz, 1), s));
+    if (nnz > 0) {
+        DBuf<uint64_t> keys;
+        DBuf<uint32_t> vals;
+        APS_TRY(keys.alloc((size_t)nnz, s));
+        APS_TRY(vals.alloc((size_t)nnz, s));
+        const int rb = std::max(1, bits_for((uint64_t)(ix->maxm - 1)));
+        k_q_keys<<<grid_for(nnz, T256), T256, 0, s>>>(qidx, erow.p, d.rank_of_dim.p, nnz, rb, keys.p, vals.p);
+        APS_LAUNCH_CHECK();
+        APS_TRY(sort_pairs(keys.p, vals.p, nnz, rb + bits_for((uint64_t)std::max(nq - 1, 0)), s));
+        k_q_gather<<<grid_for(nnz, T256), T256, 0, s>>>(keys.p, vals.p, vout.p, nnz, (1ull << rb) - 1, qa.crow.p);
+        APS_LAUNCH_CHECK();
+    }
+    APS_TRY(qa.qsplit.alloc((size_t)std::max<int64_t>(nq, 1), s));
+    APS_TRY(qa.vmeta.alloc((size_t)std::max<int64_t>(nq, 1), s));
+    if (nq > 0) {
+        k_q_split<<<grid_for(nq, T256), T256, 0, s>>>(qptr, qa.crow.p, d.mwr.p, nq, t, qa.qsplit.p, qa.vmeta.p);
+        APS_LAUNCH_CHECK();
+    }
+    return APS_OK;
+}
+
 }  // namespace aps

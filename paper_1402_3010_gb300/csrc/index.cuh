@@ -126,6 +126,25 @@ void pairs_release(aps_pairs *p);
 // Replace device pairs by one pinned host copy.
 aps_status pairs_to_host(aps_pairs *p, cudaStream_t s);
 
+// External query rows prepared against an index: components re-expressed over the index's
+// dimension ranks and sorted by rank, with |q|, maxweight(q) and the remscore boundary.
+struct QueryArrays {
+    DBuf<int2> crow;     // {rank, value} per component, rows in rank order
+    DBuf<int4> vmeta;    // {row offset, |q|, 0, 0}
+    DBuf<int32_t> qsplit;
+    DBuf<float> mw;
+    int64_t nq = 0, nnz = 0;
+};
+
+aps_status prepare_queries(const aps_index *ix, const int64_t *qptr, const int32_t *qidx, const float *qval,
+                           int32_t nq, float t, uint32_t flags, cudaStream_t s, QueryArrays &qa);
+
+// Match prepared queries against every indexed vector: pairs (query row, vector id, score)
+// with score >= t, sorted by (query, vector). Safe to call concurrently on different
+// streams (it does not modify the index).
+aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uint32_t flags, cudaStream_t s,
+                        aps_pairs *out, aps_stats *stats);
+
 // Build all index arrays for the instances whose CSRs are concatenated in (indptr, idx,
 // val) with global row pointers (indptr[0] = 0). Inputs are device pointers.
 aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_t *idx,

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstring>
 
 #include "index.cuh"
 
@@ -56,6 +57,13 @@ struct JoinParams {
     unsigned long long *counters;  // visits, candidates, verified, pairs, band
     unsigned long long *work;
     int2 *scratch;                  // per-warp lists of emitted pairs, JOIN_ECAP each
+    // query mode: items are external query rows matched against every indexed vector
+    int qmode;
+    const int2 *qcrow;    // query rows over the index's ranks
+    const int4 *qvmeta;   // {row offset, |q|, 0, 0}
+    const int32_t *qqsplit;
+    const float *qmw;
+    float qt;
 };
 
 constexpr int NWARPS = JOIN_THREADS / 32;
@@ -103,14 +111,14 @@ __device__ __forceinline__ int warp_excl_scan_int(int v, int lane, int *total) {
 
 // x's value at rank r: dense table for small ranks, binary search of x's rank-ordered row
 // otherwise.
-__device__ __noinline__ float x_at_search(int r, const int2 *__restrict__ crow, int64_t xa, int xl) {
+__device__ __noinline__ float x_at_search(int r, const int2 *__restrict__ xrow, int xl) {
     int lo = 0, hi = xl;
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        if (crow[xa + mid].x < r) lo = mid + 1; else hi = mid;
+        if (xrow[mid].x < r) lo = mid + 1; else hi = mid;
     }
     if (lo < xl) {
-        const int2 e = crow[xa + lo];
+        const int2 e = xrow[lo];
         if (e.x == r) return __int_as_float(e.y);
     }
     return 0.f;
@@ -119,9 +127,9 @@ __device__ __noinline__ float x_at_search(int r, const int2 *__restrict__ crow, 
 // x's value at rank r: dense table for small ranks, then a binary search of x's row held
 // in shared memory (xr, xs entries; xs = 0 when the row did not fit), else in global memory.
 __device__ __forceinline__ float x_at(int r, const float *xtab, int RG, const int2 *xr, int xs,
-                                      const int2 *__restrict__ crow, int64_t xa, int xl) {
+                                      const int2 *__restrict__ xrow, int xl) {
     if (r < RG) return xtab[r];
-    if (xs == 0) return x_at_search(r, crow, xa, xl);
+    if (xs == 0) return x_at_search(r, xrow, xl);
     int lo = 0, hi = xs;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -132,28 +140,28 @@ __device__ __forceinline__ float x_at(int r, const float *xtab, int RG, const in
 
 // dot(x, y') over the |y'| leading (unindexed) entries of y's rank-ordered row.
 __device__ __forceinline__ float dot_prefix(const int2 *__restrict__ yr, int ys, const float *xtab, int RG,
-                                           const int2 *xr, int xs, const int2 *__restrict__ crow, int64_t xa,
+                                           const int2 *xr, int xs, const int2 *__restrict__ xrow,
                                            int xl) {
     float acc = 0.f;
     int k = 0;
     for (; k + 2 <= ys; k += 2) {
         const int2 e0 = yr[k], e1 = yr[k + 1];
-        acc = fmaf(x_at(e0.x, xtab, RG, xr, xs, crow, xa, xl), __int_as_float(e0.y), acc);
-        acc = fmaf(x_at(e1.x, xtab, RG, xr, xs, crow, xa, xl), __int_as_float(e1.y), acc);
+        acc = fmaf(x_at(e0.x, xtab, RG, xr, xs, xrow, xl), __int_as_float(e0.y), acc);
+        acc = fmaf(x_at(e1.x, xtab, RG, xr, xs, xrow, xl), __int_as_float(e1.y), acc);
     }
     if (k < ys) {
         const int2 e0 = yr[k];
-        acc = fmaf(x_at(e0.x, xtab, RG, xr, xs, crow, xa, xl), __int_as_float(e0.y), acc);
+        acc = fmaf(x_at(e0.x, xtab, RG, xr, xs, xrow, xl), __int_as_float(e0.y), acc);
     }
     return acc;
 }
 
 // float64 dot product of two rank-ordered rows (used inside the decision band).
-__device__ double dot64(const int2 *__restrict__ crow, int64_t xa, int xl, int64_t ya, int yl) {
+__device__ double dot64(const int2 *__restrict__ xr, int xl, const int2 *__restrict__ yr, int yl) {
     double s = 0.0;
     int p = 0, q = 0;
     while (p < xl && q < yl) {
-        const int2 a = crow[xa + p], b = crow[ya + q];
+        const int2 a = xr[p], b = yr[q];
         if (a.x == b.x) {
             s += (double)__int_as_float(a.y) * (double)__int_as_float(b.y);
             p++;
@@ -202,15 +210,17 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
         gsync(G, g, GT);
         const int64_t it = bc[0];
         if (it >= P.item_end) break;
-        const int64_t x = P.items[it];
-        const InstDesc I = P.inst[P.vinst[x]];
-        const int32_t lx = (int32_t)(x - I.vbase);
-        const int4 xm = P.vmeta[x];
-        const int64_t xa = xm.x;
+        // x: a vector of the set (self-join: candidates are the later ids of its instance)
+        // or an external query (all indexed vectors are candidates)
+        const int64_t x = P.qmode ? it : (int64_t)P.items[it];
+        const InstDesc I = P.inst[P.qmode ? 0 : P.vinst[x]];
+        const int32_t lx = P.qmode ? -1 : (int32_t)(x - I.vbase);
+        const int4 xm = P.qmode ? P.qvmeta[x] : P.vmeta[x];
+        const int2 *xrow = (P.qmode ? P.qcrow : P.crow) + xm.x;
         const int32_t xl = xm.y;
-        const int32_t qs = f_remscore ? P.qsplit[x] : 0;
-        const float mwx = P.mw[x];
-        const float t = I.t;
+        const int32_t qs = f_remscore ? (P.qmode ? P.qqsplit[x] : P.qsplit[x]) : 0;
+        const float mwx = P.qmode ? P.qmw[x] : P.mw[x];
+        const float t = P.qmode ? P.qt : I.t;
         const float beta = fmaxf(1e-5f, (float)(xl + 2) * 1.1920929e-7f);  // (|x|+2) * 2^-23
         // no component reaches remscore >= t: x can create no candidate at all
         if (f_remscore ? qs >= xl : xl == 0) continue;
@@ -227,7 +237,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
         gsync(G, g, GT);
         const int xs = xl <= XG ? xl : 0;  // x's row in shared memory when it fits
         for (int c = gt; c < xl; c += GT) {
-            const int2 e = P.crow[xa + c];
+            const int2 e = xrow[c];
             if (e.x < RG) xtab[e.x] = __int_as_float(e.y);
             if (c < xs) xr[c] = e;
         }
@@ -248,7 +258,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                 const bool ph0 = cp < ncreate;
                 if (cp < xl) {
                     const int c = ph0 ? qs + cp : cp - ncreate;
-                    const int2 e = P.crow[xa + c];
+                    const int2 e = xrow[c];
                     const int64_t R = (int64_t)I.rbase + e.x;
                     xv = __int_as_float(e.y);
                     int64_t ls = P.lptr[R], le = P.lptr[R + 1];
@@ -385,13 +395,13 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                             if (ok) {
                                 if (ys > 0) {
                                     n_verified++;
-                                    sc = v + dot_prefix(P.crow + ym.x, ys, xtab, RG, xr, xs, P.crow, xa, xl);
+                                    sc = v + dot_prefix(P.crow + ym.x, ys, xtab, RG, xr, xs, xrow, xl);
                                 }
                                 if (sc >= t + beta) {
                                     emit = true;
                                 } else if (sc > t - beta) {
                                     n_band++;
-                                    const double s64 = dot64(P.crow, xa, xl, ym.x, ym.y);
+                                    const double s64 = dot64(xrow, xl, P.crow + ym.x, ym.y);
                                     emit = s64 >= (double)t;
                                     sc = (float)s64;
                                 }
@@ -415,7 +425,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     wcnt[k] = (int32_t)tot;
                     tot += c;
                 }
-                const int64_t qw = I.qwbase + (int64_t)lx * I.nw + w;
+                const int64_t qw = P.qmode ? x * I.nw + w : I.qwbase + (int64_t)lx * I.nw + w;
                 P.cntq[qw] = (int32_t)tot;
                 int64_t b = 0, wr = 0;
                 if (tot > 0) {
@@ -426,7 +436,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                         S.src = b;
                         S.qw = qw;
                         S.cnt = (int32_t)tot;
-                        S.i = lx;
+                        S.i = P.qmode ? (int32_t)x : lx;
                         P.segs[sid] = S;
                         wr = 1;
                     }
@@ -546,6 +556,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
             P.counters = ctr.p;
             P.work = ctr.p + 8 + c;
             P.scratch = scratch.p;
+            P.qmode = 0;
             const int64_t nitems = e - b;
             const int64_t groups_needed = (nitems + Gs[c] - 1) / Gs[c];
             const int grid = (int)std::min<int64_t>(sms, std::max<int64_t>(groups_needed, 1));
@@ -786,6 +797,7 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
         P.counters = ctr;
         P.work = ctr + 8 + c;
         P.scratch = elists;
+        P.qmode = 0;
         const int64_t groups_needed = (e - b + Gs[c] - 1) / Gs[c];
         const int grid = (int)std::min<int64_t>(grid_max, std::max<int64_t>(groups_needed, 1));
         join_kernel<<<grid, JOIN_THREADS, group_bytes(Gs[c]) * Gs[c], s>>>(P);
@@ -813,6 +825,133 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
         APS_LAUNCH_CHECK();
     }
     APS_CUDA(cudaStreamSynchronize(s));
+    return APS_OK;
+}
+
+// ------------------------------------------------------------------ external queries
+aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uint32_t flags, cudaStream_t s,
+                        aps_pairs *out, aps_stats *stats) {
+    const IndexArrays &d = ix->d;
+    const InstDesc &I = ix->inst_h[0];
+    const int sms = num_sms();
+    const int64_t nq = qa.nq;
+    const int64_t nqw = std::max<int64_t>(nq * (int64_t)std::max(I.nw, 1), 1);
+    const int G = I.G;
+    const int Gs[4] = {1, 2, 4, 8};
+    int need = 0;
+    for (int c = 0; c < 4; c++) need = std::max(need, group_bytes(Gs[c]) * Gs[c]);
+    APS_CUDA(cudaFuncSetAttribute(join_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
+    cudaEvent_t ev[3];
+    for (int i = 0; i < 3; i++) APS_CUDA(cudaEventCreate(&ev[i]));
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int i = 0; i < 3; i++) cudaEventDestroy(e[i]);
+        }
+    } evg{ev};
+    const int grid = (int)std::min<int64_t>(sms, std::max<int64_t>((nq + G - 1) / G, 1));
+    DBuf<int32_t> cntq;
+    DBuf<unsigned long long> ctr;
+    DBuf<int2> scratch, stage;
+    DBuf<Segment> segs;
+    APS_TRY(cntq.alloc((size_t)nqw, s));
+    APS_TRY(ctr.alloc(16, s));
+    APS_TRY(scratch.alloc((size_t)grid * NWARPS * JOIN_ECAP, s));
+    APS_TRY(segs.alloc((size_t)nqw, s));
+    int64_t stage_cap = std::max<int64_t>({nq * 64, (int64_t)1 << 16});
+    unsigned long long ch[16];
+    for (int attempt = 0; attempt < 2; attempt++) {
+        APS_TRY(stage.alloc((size_t)stage_cap, s));
+        APS_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(ch), s));
+        APS_CUDA(cudaMemsetAsync(cntq.p, 0, sizeof(int32_t) * nqw, s));
+        APS_CUDA(cudaEventRecord(ev[0], s));
+        if (nq > 0) {
+            JoinParams P;
+            memset(&P, 0, sizeof(P));
+            P.inst = d.inst.p;
+            P.vinst = d.vinst.p;
+            P.items = nullptr;
+            P.item_begin = 0;
+            P.item_end = nq;
+            P.G = G;
+            P.crow = d.crow.p;
+            P.vmeta = d.vmeta.p;
+            P.pnorm = d.pnorm.p;
+            P.qsplit = d.qsplit.p;
+            P.mw = d.mw.p;
+            P.lptr = d.lptr.p;
+            P.wptr = d.wptr.p;
+            P.post = d.post.p;
+            P.flags = flags & (APS_NO_MINSIZE | APS_NO_REMSCORE | APS_NO_UPPERBOUND);
+            P.stage = stage.p;
+            P.stage_cap = stage_cap;
+            P.stage_count = ctr.p + 5;
+            P.segs = segs.p;
+            P.seg_cap = nqw;
+            P.seg_count = ctr.p + 6;
+            P.cntq = cntq.p;
+            P.counters = ctr.p;
+            P.work = ctr.p + 8;
+            P.scratch = scratch.p;
+            P.qmode = 1;
+            P.qcrow = qa.crow.p;
+            P.qvmeta = qa.vmeta.p;
+            P.qqsplit = qa.qsplit.p;
+            P.qmw = qa.mw.p;
+            P.qt = t;
+            join_kernel<<<grid, JOIN_THREADS, group_bytes(G) * G, s>>>(P);
+            APS_LAUNCH_CHECK();
+        }
+        APS_CUDA(cudaEventRecord(ev[1], s));
+        APS_CUDA(cudaMemcpyAsync(ch, ctr.p, sizeof(ch), cudaMemcpyDeviceToHost, s));
+        APS_CUDA(cudaStreamSynchronize(s));
+        if ((int64_t)ch[5] <= stage_cap) break;
+        stage_cap = (int64_t)ch[5];
+    }
+    const int64_t npairs = (int64_t)ch[5], nseg = (int64_t)ch[6];
+    DBuf<int64_t> qwoff;
+    APS_TRY(qwoff.alloc((size_t)nqw + 1, s));
+    APS_TRY(scan_exclusive(cntq.p, qwoff.p, nqw, s));
+    PairsAlloc *pa = new PairsAlloc();
+    pa->stream = s;
+    const size_t seg4 = ((size_t)npairs * 4 + 127) & ~(size_t)127;
+    aps_status st = dalloc(&pa->block, std::max<size_t>(3 * seg4, 256), s);
+    if (st != APS_OK) {
+        delete pa;
+        return st;
+    }
+    char *blk = static_cast<char *>(pa->block);
+    int32_t *oi = reinterpret_cast<int32_t *>(blk);
+    int32_t *oj = reinterpret_cast<int32_t *>(blk + seg4);
+    float *os = reinterpret_cast<float *>(blk + 2 * seg4);
+    if (nseg > 0) {
+        k_gather<<<(unsigned)std::min<int64_t>(nseg, (int64_t)sms * 32), 256, 0, s>>>(segs.p, nseg, stage.p, qwoff.p,
+                                                                                      oi, oj, os);
+        APS_LAUNCH_CHECK();
+    }
+    APS_CUDA(cudaEventRecord(ev[2], s));
+    APS_CUDA(cudaEventSynchronize(ev[2]));
+    if (stats) {
+        float mj = 0, mo = 0;
+        cudaEventElapsedTime(&mj, ev[0], ev[1]);
+        cudaEventElapsedTime(&mo, ev[1], ev[2]);
+        memset(stats, 0, sizeof(*stats));
+        stats->visits = (int64_t)ch[0];
+        stats->candidates = (int64_t)ch[1];
+        stats->verified = (int64_t)ch[2];
+        stats->pairs = (int64_t)ch[3];
+        stats->band = (int64_t)ch[4];
+        stats->evaluations = nq * (int64_t)I.n;
+        stats->ms_join = mj;
+        stats->ms_sort = mo;
+    }
+    out->count = npairs;
+    out->i = oi;
+    out->j = oj;
+    out->score = os;
+    out->on_device = 1;
+    out->_reserved = 0;
+    out->_priv = pa;
     return APS_OK;
 }
 
