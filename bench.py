@@ -51,9 +51,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=600, help="queries in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sparse", choices=["sparse", "dense"],
+    ap.add_argument("--workload", default="sparse", choices=["sparse", "dense", "batched", "serving"],
                     help="sparse: the 200k-vector sparse self-join (default line); dense: the 200k x 256 "
-                         "embedding self-join on the tensor cores")
+                         "embedding self-join on the tensor cores; batched: 512 independent sparse "
+                         "instances; serving: query batches against a 1M-vector resident index")
+    ap.add_argument("--serve-batches", type=int, default=160)
+    ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--d", type=int, default=256)
     return ap.parse_args()
 
@@ -438,6 +441,178 @@ def run_dense(args, rank, world):
     return line
 
 
+BATCHED_WORKLOAD = ("batched sparse all-pairs: 512 independent instances, n log-uniform in [100, 20000], m=50000, "
+                    "|x| ~ Poisson(30) in [1,300], Zipf(1.1) ids, U(0,1] weights, t ~ U(0.6, 0.9)")
+SERVING_WORKLOAD = ("serving: resident index of 1M sparse vectors (m=200000, power-law |x| mean 40, Zipf(1.0), "
+                    "log-normal weights), query batches of log-uniform size 1-4096, t=0.75")
+
+
+def _sparse_roofline(st, ms):
+    peak, kind = peaks()
+    alg = 8 * st["visits"] + 8 * st["candidates"] + 16 * st["verified"] + 8 * st["pairs"]
+    ach = alg / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "join_kernel", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_kind": kind + " (hbm_gbs, copy bandwidth)", "traffic": None,
+            "alg_bytes_per_launch": alg, "ms_per_launch": ms}
+
+
+def run_batched(args):
+    import torch
+
+    import oracle
+    import paper_1402_3010_gb300 as aps
+    import synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    aps.load()
+    ro, c, m, t = synth.config_batched_csr()
+    ns = np.diff(ro)
+    evals = int((ns * (ns - 1) // 2).sum())
+    ip, ix, vv = (torch.from_numpy(a).to(dev) for a in (c.indptr, c.idx, c.val))
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        outs, st = aps.aps_batch_all_pairs_csr(ro, ip, ix, vv, m, t, 0, stream)
+        cnt = sum(int(o.count) for o in outs)
+        for o in outs:
+            aps.aps_pairs_free(o)
+        return st, cnt
+
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        st, cnt = step()
+    clocks = Clocks(0)
+    clocks.start()
+    jm = []
+    l0 = aps.aps_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        st, cnt = step()
+        jm.append(st["ms_join"])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    launches = aps.aps_launch_count() - l0
+    clk = clocks.stop()
+    line = {
+        "metric": METRIC, "value": evals * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": BATCHED_WORKLOAD, "instances": len(ns), "total_n": int(ns.sum()), "nnz": c.nnz,
+                   "parallelism": "single GPU", "l2": "256 MB buffer written between steps (L2 flush)",
+                   "pairs_per_step": cnt, "evaluations_per_step": evals},
+        "roofline": _sparse_roofline(st, statistics.mean(jm)),
+        "phases_ms": {"build": st["ms_build"], "join": st["ms_join"], "output": st["ms_sort"],
+                      "call": st["ms_total"]},
+        "work": {k: st[k] for k in ("visits", "candidates", "verified", "pairs", "band")},
+        "gpu_launches": launches, "e2e": None, "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        sel = np.random.default_rng(11).choice(len(ns), 24, replace=False)
+        t0 = time.perf_counter()
+        ev = 0
+        for r in sel:
+            a, b = int(ro[r]), int(ro[r + 1])
+            ip_r = c.indptr[a:b + 1] - c.indptr[a]
+            cr = synth.SparseCSR(ip_r, c.idx[c.indptr[a]:c.indptr[b]], c.val[c.indptr[a]:c.indptr[b]], b - a,
+                                 int(m[r]))
+            oracle.all_pairs(cr, float(t[r]), oracle.ALL_PAIRS_2)
+            ev += (b - a) * (b - a - 1) // 2
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"sequential all-pairs-2 (C, FP64) on 24 random instances ({ev} "
+                                          f"evaluations) in {dt:.2f} s"}
+    return line
+
+
+def run_serving(args):
+    import torch
+
+    import paper_1402_3010_gb300 as aps
+    import synth
+
+    torch.cuda.set_device(0)
+    aps.load()
+    c, t = synth.config_serving()
+    t = float(np.float32(t))
+    h = aps.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, t, aps.QUERYABLE)
+    rng = np.random.default_rng(57)
+    sizes = np.clip(np.exp(rng.uniform(0.0, math.log(4096.0), size=args.serve_batches)).astype(np.int64), 1, 4096)
+    q = synth.serving_queries(int(sizes.sum()))
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    batches = []
+    for a, b in zip(offs[:-1], offs[1:]):
+        ip = (q.indptr[a:b + 1] - q.indptr[a]).astype(np.int64)
+        batches.append((ip, q.idx[q.indptr[a]:q.indptr[b]].copy(), q.val[q.indptr[a]:q.indptr[b]].copy(), int(b - a)))
+
+    def run(arrivals):
+        """Submit batch k at arrivals[k] seconds (all at once when None); latency = result
+        in host memory - arrival."""
+        sv = aps.aps_server_create(h, 96 << 30, args.slots)
+        lat, pairs = [], 0
+        try:
+            t0 = time.perf_counter()
+            pending = {}
+            k = 0
+            while k < len(batches) or pending:
+                now = time.perf_counter() - t0
+                while k < len(batches) and (arrivals is None or arrivals[k] <= now):
+                    ip, ix, vv, nq = batches[k]
+                    arr = now if arrivals is None else arrivals[k]
+                    pending[aps.aps_stream_submit(sv, ip, ix, vv, nq, t)] = arr
+                    k += 1
+                done = []
+                for tk, arr in pending.items():
+                    p = aps.aps_stream_poll(sv, tk, 0)
+                    if p is not None:
+                        lat.append(time.perf_counter() - t0 - arr)
+                        pairs += int(p.count)
+                        aps.aps_pairs_free(p)
+                        done.append(tk)
+                for tk in done:
+                    del pending[tk]
+                if not done:
+                    time.sleep(0.0001)
+            total = time.perf_counter() - t0
+        finally:
+            aps.aps_server_free(sv)
+        return total, np.array(lat), pairs
+
+    run(None)  # warm-up
+    clocks = Clocks(0)
+    clocks.start()
+    tsat, lsat, pairs = run(None)
+    clk = clocks.stop()
+    qps = offs[-1] / tsat
+    loads = {}
+    for frac in (0.5, 0.8):
+        gaps = np.random.default_rng(58).exponential(1.0 / (frac * len(batches) / tsat), size=len(batches))
+        tt, ll, _ = run(np.cumsum(gaps))
+        loads[f"{int(frac * 100)}%"] = {"p50_ms": 1000 * float(np.percentile(ll, 50)),
+                                        "p99_ms": 1000 * float(np.percentile(ll, 99)),
+                                        "batches_per_s": len(batches) / tt}
+    aps.aps_index_free(h)
+    evals = int(offs[-1]) * c.n
+    return {
+        "metric": METRIC, "value": evals / tsat, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": 1000 * tsat, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": SERVING_WORKLOAD, "index_n": c.n, "index_nnz": c.nnz, "batches": len(batches),
+                   "queries": int(offs[-1]), "slots": args.slots, "t": t, "parallelism": "single GPU",
+                   "pairs": pairs},
+        "serving": {"saturated_queries_per_s": qps,
+                    "saturated_p50_ms": 1000 * float(np.percentile(lsat, 50)),
+                    "saturated_p99_ms": 1000 * float(np.percentile(lsat, 99)), "poisson_load": loads},
+        "clocks": clk, "e2e": None,
+    }
+
+
 def run_reference(args, rank):
     """The reference arm: the CPU oracle (no upstream implementation exists), on rank 0."""
     if rank != 0:
@@ -482,6 +657,10 @@ def main():
         line = run_reference(args, rank)
     elif args.workload == "dense":
         line = run_dense(args, rank, world)
+    elif args.workload == "batched":
+        line = run_batched(args)
+    elif args.workload == "serving":
+        line = run_serving(args)
     else:
         line = run_aps(args, rank, world)
     if line is not None:

@@ -182,6 +182,17 @@ typedef struct aps_instance {
 aps_status aps_batch_all_pairs(int32_t k, const aps_instance *inst, uint32_t flags,
                                void *stream, aps_pairs *outs, aps_stats *stats);
 
+/* The batched self-join over one concatenated CSR: instance r owns rows
+ * [row_offsets[r], row_offsets[r+1]) (host array of k+1 entries, row_offsets[0] = 0);
+ * indptr (row_offsets[k]+1 entries, global: indptr[0] = 0), idx, val as in
+ * aps_build_index (device pointers with APS_DEVICE_PTRS, dimension ids local to each
+ * instance, in [0, m[r])); m and t are host arrays of k entries. Results and ownership as
+ * in aps_batch_all_pairs. Avoids per-instance copies when the batch is device-resident. */
+aps_status aps_batch_all_pairs_csr(int32_t k, const int64_t *row_offsets, const int64_t *indptr,
+                                   const int32_t *idx, const float *val, const int32_t *m,
+                                   const float *t, uint32_t flags, void *stream, aps_pairs *outs,
+                                   aps_stats *stats);
+
 /* ---- dense embeddings ----------------------------------------------------------- */
 /* All pairs (i < j) of n unit vectors X[n, d] (float32, row-major) with X_i . X_j >= t:
  * the S = D.D^T view of Sec. 2.1 computed as a BF16 tensor-core product with float32

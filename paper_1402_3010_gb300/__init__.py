@@ -17,7 +17,7 @@ __all__ = [
     "APSError", "load", "lib_path",
     "aps_build_index", "aps_all_pairs", "aps_query", "aps_index_export", "aps_index_info",
     "aps_index_stats", "aps_index_free", "aps_pairs_free", "aps_pairs_copy_to",
-    "aps_batch_all_pairs", "aps_all_pairs_dense", "aps_server_create", "aps_stream_submit",
+    "aps_batch_all_pairs", "aps_batch_all_pairs_csr", "aps_all_pairs_dense", "aps_server_create", "aps_stream_submit",
     "aps_stream_poll", "aps_stream_cancel", "aps_server_free", "aps_last_error", "aps_version",
     "aps_debug_fail_alloc", "aps_launch_count", "aps_all_pairs_noalloc", "pairs_to_numpy", "pairs_to_torch",
     "DEVICE_PTRS", "NORMALIZE", "QUERYABLE", "NO_PARTIAL_INDEX", "NO_MINSIZE", "NO_REMSCORE",
@@ -105,6 +105,8 @@ def load():
             "aps_pairs_copy_to": (_i32, [ctypes.POINTER(aps_pairs), _P, _P, _P, _P]),
             "aps_batch_all_pairs": (_i32, [_i32, ctypes.POINTER(aps_instance), _u32, _P,
                                            ctypes.POINTER(aps_pairs), ctypes.POINTER(aps_stats)]),
+            "aps_batch_all_pairs_csr": (_i32, [_i32, _P, _P, _P, _P, _P, _P, _u32, _P, ctypes.POINTER(aps_pairs),
+                                               ctypes.POINTER(aps_stats)]),
             "aps_all_pairs_dense": (_i32, [_P, _i32, _i32, _f32, _u32, _P, ctypes.POINTER(aps_pairs),
                                            ctypes.POINTER(aps_stats)]),
             "aps_server_create": (_i32, [_P, ctypes.c_size_t, _i32, ctypes.POINTER(_P)]),
@@ -315,6 +317,25 @@ def aps_batch_all_pairs(instances, flags: int = 0, stream=None):
     rc = lib.aps_batch_all_pairs(k, arr, int(flags) | f, _stream_ptr(stream), outs, ctypes.byref(st))
     del keep
     _check(rc, "aps_batch_all_pairs")
+    return list(outs), st.as_dict()
+
+
+def aps_batch_all_pairs_csr(row_offsets, indptr, idx, val, m, t, flags: int = 0, stream=None):
+    """One concatenated CSR (NumPy host or torch device arrays) with instance row offsets
+    (host int64 [k+1]), per-instance m (int32 [k]) and t (float32 [k]).
+    Returns (list of aps_pairs, stats dict)."""
+    lib = load()
+    ro = np.ascontiguousarray(row_offsets, dtype=np.int64)
+    mm = np.ascontiguousarray(m, dtype=np.int32)
+    tt = np.ascontiguousarray(t, dtype=np.float32)
+    k = int(ro.size - 1)
+    (p0, p1, p2), f, keep = _csr_args(indptr, idx, val)
+    outs = (aps_pairs * k)()
+    st = aps_stats()
+    rc = lib.aps_batch_all_pairs_csr(k, ro.ctypes.data, p0, p1, p2, mm.ctypes.data, tt.ctypes.data, int(flags) | f,
+                                     _stream_ptr(stream), outs, ctypes.byref(st))
+    del keep
+    _check(rc, "aps_batch_all_pairs_csr")
     return list(outs), st.as_dict()
 
 

@@ -376,6 +376,88 @@ aps_status aps_batch_all_pairs(int32_t k, const aps_instance *inst, uint32_t fla
     return st;
 }
 
+aps_status aps_batch_all_pairs_csr(int32_t k, const int64_t *row_offsets, const int64_t *indptr, const int32_t *idx,
+                                   const float *val, const int32_t *m, const float *t, uint32_t flags, void *stream,
+                                   aps_pairs *outs, aps_stats *stats) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (k < 1 || !row_offsets || !indptr || !m || !t || !outs) {
+        set_error("need k >= 1 and non-NULL row_offsets, indptr, m, t, outs");
+        return APS_EINVAL;
+    }
+    for (int i = 0; i < k; i++) memset(&outs[i], 0, sizeof(aps_pairs));
+    if (row_offsets[0] != 0) {
+        set_error("row_offsets[0] must be 0");
+        return APS_EINVAL;
+    }
+    std::vector<InstDesc> desc((size_t)k);
+    for (int i = 0; i < k; i++) {
+        const int64_t n = row_offsets[i + 1] - row_offsets[i];
+        if (n < 0 || n >= (1ll << 31) || m[i] < 1) {
+            set_error("instance %d: need 0 <= n < 2^31 and m >= 1", i);
+            return APS_EINVAL;
+        }
+        APS_TRY(check_threshold(t[i]));
+        memset(&desc[i], 0, sizeof(InstDesc));
+        desc[i].n = (int32_t)n;
+        desc[i].m = m[i];
+        desc[i].t = t[i];
+    }
+    const int64_t N = row_offsets[k];
+    aps_index *ix = new (std::nothrow) aps_index();
+    if (!ix) return APS_ENOMEM;
+    ix->flags = flags;
+    ix->stream = s;
+    cudaGetDevice(&ix->device);
+    cudaEvent_t e0, e1, e2;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+    cudaEventRecord(e0, s);
+    aps_status st;
+    std::vector<int64_t> offs;
+    {
+        HostCsrCopy c;
+        const int64_t *dp;
+        const int32_t *di;
+        const float *dv;
+        st = stage_csr(indptr, idx, val, N, flags, s, c, &dp, &di, &dv);
+        if (st == APS_OK) st = build_index_device(ix, dp, di, dv, desc, s);
+    }
+    cudaEventRecord(e1, s);
+    aps_pairs all;
+    memset(&all, 0, sizeof(all));
+    if (st == APS_OK) st = join_all_pairs(ix, flags, &all, &offs);
+    if (st == APS_OK && (flags & APS_HOST_OUTPUT)) st = pairs_to_host(&all, s);
+    cudaEventRecord(e2, s);
+    cudaEventSynchronize(e2);
+    if (st == APS_OK) {
+        float mb = 0, mt = 0;
+        cudaEventElapsedTime(&mb, e0, e1);
+        cudaEventElapsedTime(&mt, e0, e2);
+        ix->stats.ms_build = mb;
+        ix->stats.ms_total = mt;
+        if (stats) *stats = ix->stats;
+        static_cast<PairsAlloc *>(all._priv)->refs = k;
+        for (int i = 0; i < k; i++) {
+            aps_pairs &o = outs[i];
+            o.count = offs[i + 1] - offs[i];
+            o.i = all.i + offs[i];
+            o.j = all.j + offs[i];
+            o.score = all.score + offs[i];
+            o.on_device = all.on_device;
+            o._priv = all._priv;
+        }
+    } else {
+        pairs_release(&all);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    delete ix;
+    cudaStreamSynchronize(s);
+    return st;
+}
+
 aps_status aps_all_pairs_dense(const float *X, int32_t n, int32_t d, float t, uint32_t flags, void *stream,
                                aps_pairs *out, aps_stats *stats) {
     if (!out) {

@@ -90,9 +90,22 @@ def power_law_lengths(rng, n, alpha, lo, hi):
     return (lo + np.searchsorted(c, u, side="left")).astype(np.int64)
 
 
-def _distinct_zipf_rows(rng, lengths, m, s):
+def _distinct_zipf_rows(rng, lengths, m, s, chunk=262144):
     """For each row draw bounded-Zipf ranks (0-based) until ``lengths[r]`` distinct ranks
-    are collected, i.e. sampling without replacement in draw order."""
+    are collected, i.e. sampling without replacement in draw order. Rows are drawn in
+    chunks of ``chunk`` rows (keeps the sort keys within 63 bits)."""
+    lengths = np.asarray(lengths, dtype=np.int64)
+    if lengths.size > chunk:
+        rows, ranks = [], []
+        for a in range(0, lengths.size, chunk):
+            r, k = _distinct_zipf_rows_chunk(rng, lengths[a : a + chunk], m, s)
+            rows.append(r + a)
+            ranks.append(k)
+        return np.concatenate(rows), np.concatenate(ranks)
+    return _distinct_zipf_rows_chunk(rng, lengths, m, s)
+
+
+def _distinct_zipf_rows_chunk(rng, lengths, m, s):
     n = len(lengths)
     lengths = np.asarray(lengths, dtype=np.int64)
     if np.any(lengths > m):
@@ -276,6 +289,33 @@ def config_batched(seed: int = 4, k: int = 512, n_lo: int = 100, n_hi: int = 200
     return out
 
 
+def config_batched_csr(seed: int = 4, k: int = 512, n_lo: int = 100, n_hi: int = 20000, m: int = 50_000):
+    """The batched workload as one concatenated CSR: instance r owns rows
+    [row_offsets[r], row_offsets[r+1]); n log-uniform in [n_lo, n_hi], |x| ~ Poisson(30)
+    clipped to [1,300], Zipf(1.1) ids (one rank -> id permutation shared by the instances;
+    dimension ids are local to each instance), U(0,1] weights, L2-normalised;
+    t ~ U(0.6, 0.9) rounded to float32. Returns (row_offsets, SparseCSR, m[k], t[k])."""
+
+    def make():
+        rng = np.random.default_rng(seed)
+        ns = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=k)).astype(np.int64)
+        ts = rng.uniform(0.6, 0.9, size=k).astype(np.float32)
+        N = int(ns.sum())
+        lengths = poisson_lengths(rng, N, 30, 1, 300)
+        c = sparse_vectors(N, m, lengths, 1.1, "uniform", seed, rng=rng)
+        ro = np.zeros(k + 1, dtype=np.int64)
+        np.cumsum(ns, out=ro[1:])
+        return SparseCSR(np.concatenate([c.indptr, ro, ts.view(np.int32).astype(np.int64)]), c.idx, c.val, N, m)
+
+    z = _cached(f"batched-v1-s{seed}-k{k}-{n_lo}-{n_hi}-m{m}", make)
+    N = z.n
+    indptr = z.indptr[: N + 1]
+    ro = z.indptr[N + 1 : N + 2 + k]
+    ts = z.indptr[N + 2 + k :].astype(np.int32).view(np.float32)
+    c = SparseCSR(indptr, z.idx, z.val, N, m)
+    return ro, c, np.full(k, m, dtype=np.int32), ts
+
+
 def _serving_perm(seed: int, m: int) -> np.ndarray:
     return np.random.default_rng([seed, 7919]).permutation(m)
 
@@ -285,8 +325,11 @@ def config_serving(seed: int = 5, n: int = 1_000_000, m: int = 200_000):
     Zipf(1.0) ids, log-normal(0,1) weights, L2-normalised; t=0.75."""
     rng = np.random.default_rng(seed)
     lengths = power_law_lengths(rng, n, ALPHA_MEAN40, 1, min(2000, m))
-    csr = sparse_vectors(n, m, lengths, 1.0, "lognormal", seed, rng=rng, perm=_serving_perm(seed, m))
-    return csr, 0.75
+
+    def make():
+        return sparse_vectors(n, m, lengths, 1.0, "lognormal", seed, rng=rng, perm=_serving_perm(seed, m))
+
+    return _cached(f"serving-v1-s{seed}-n{n}-m{m}", make), 0.75
 
 
 def serving_queries(nq: int, index_seed: int = 5, m: int = 200_000, qseed: int = 55) -> SparseCSR:

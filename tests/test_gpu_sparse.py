@@ -335,3 +335,34 @@ def test_batched_instances_match_per_instance_oracle(aps):
     finally:
         for p in outs:
             A.aps_pairs_free(p)
+
+
+def test_batched_concatenated_csr_matches_per_instance_oracle(aps):
+    import paper_1402_3010_gb300 as A
+
+    rng = np.random.default_rng(71)
+    k = 40
+    ns = np.exp(rng.uniform(np.log(3), np.log(12000), size=k)).astype(np.int64)
+    ns[5] = 0
+    ts = rng.uniform(0.6, 0.9, size=k).astype(np.float32)
+    lengths = synth.poisson_lengths(rng, int(ns.sum()), 10, 1, 60)
+    c = synth.sparse_vectors(int(ns.sum()), 2000, lengths, 1.1, "uniform", 71, rng=rng)
+    ro = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    m = np.full(k, 2000, np.int32)
+    import torch
+
+    dev = [torch.from_numpy(a).cuda() for a in (c.indptr, c.idx, c.val)]
+    outs, st = A.aps_batch_all_pairs_csr(ro, *dev, m, ts)
+    try:
+        total = 0
+        for r in range(k):
+            a, b = int(ro[r]), int(ro[r + 1])
+            ip = c.indptr[a:b + 1] - c.indptr[a]
+            cr = synth.SparseCSR(ip, c.idx[c.indptr[a]:c.indptr[b]], c.val[c.indptr[a]:c.indptr[b]], b - a, 2000)
+            i, j, s = A.pairs_to_numpy(outs[r])
+            compare(i, j, s, oracle.bruteforce(cr, float(ts[r])), float(ts[r]), max(b - a, 1), csr=cr)
+            total += len(i)
+        assert st["pairs"] == total
+    finally:
+        for o in outs:
+            A.aps_pairs_free(o)
