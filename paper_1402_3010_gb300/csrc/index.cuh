@@ -20,6 +20,8 @@
 //               only for instances with > 1 window
 #pragma once
 
+#include <mutex>
+
 #include "aps_internal.cuh"
 
 namespace aps {
@@ -111,6 +113,7 @@ struct aps_index {
     int64_t hint_pairs = 0;
     int64_t hint_segs = 0;
     aps_stats stats{};
+    std::mutex stats_mu;  // queries may run concurrently (serving slots)
 };
 
 namespace aps {

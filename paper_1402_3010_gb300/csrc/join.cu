@@ -156,25 +156,6 @@ __device__ __forceinline__ float dot_prefix(const int2 *__restrict__ yr, int ys,
     return acc;
 }
 
-// float64 dot product of two rank-ordered rows (used inside the decision band).
-__device__ double dot64(const int2 *__restrict__ xr, int xl, const int2 *__restrict__ yr, int yl) {
-    double s = 0.0;
-    int p = 0, q = 0;
-    while (p < xl && q < yl) {
-        const int2 a = xr[p], b = yr[q];
-        if (a.x == b.x) {
-            s += (double)__int_as_float(a.y) * (double)__int_as_float(b.y);
-            p++;
-            q++;
-        } else if (a.x < b.x) {
-            p++;
-        } else {
-            q++;
-        }
-    }
-    return s;
-}
-
 __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int G = P.G;
@@ -243,7 +224,8 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
         }
         gsync(G, g, GT);
 
-        for (int w = (lx + 1) / I.W; w < I.nw; w++) {
+        const int wfirst = (lx + 1) / I.W;
+        for (int w = wfirst; w < I.nw; w++) {
             const int w0 = w * I.W;
             const int wn = min(I.W, I.n - w0);
             const int lo = max(0, lx + 1 - w0);
@@ -377,35 +359,75 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                 while (tail - head >= 32 || (sb + 64 >= se && tail > head)) {
                     const int nb = min(32, tail - head);
                     bool emit = false;
-                    float sc = 0.f;
+                    float sc = 0.f, v = 0.f;
                     int s = 0;
+                    int4 ym = make_int4(0, 0, 0, 0);
+                    // 0: rejected, 1: score known, 2: short dot(x, y') left, 3: long dot left
+                    int stage = 0;
                     if (lane < nb) {
                         s = ring[(head + lane) & (JOIN_RING - 1)];
-                        const float v = A[s];
+                        v = A[s];
                         A[s] = 0.f;
                         const int64_t gy = I.vbase + w0 + s;
                         sc = v;
                         // dot(x, y') <= ||y'||_2: most candidates stop here, on a 4-byte load
                         if (v + __ldg(&P.pnorm[gy]) > t - beta) {
-                            const int4 ym = __ldg(&P.vmeta[gy]);
+                            ym = __ldg(&P.vmeta[gy]);
                             const int ys = ym.z;
                             bool ok = true;
                             if (ys > 0 && f_upper)
                                 ok = v + (float)min(ys, xl) * mwx * __int_as_float(ym.w) >= t - beta;
-                            if (ok) {
-                                if (ys > 0) {
-                                    n_verified++;
-                                    sc = v + dot_prefix(P.crow + ym.x, ys, xtab, RG, xr, xs, xrow, xl);
-                                }
-                                if (sc >= t + beta) {
-                                    emit = true;
-                                } else if (sc > t - beta) {
-                                    n_band++;
-                                    const double s64 = dot64(xrow, xl, P.crow + ym.x, ym.y);
-                                    emit = s64 >= (double)t;
-                                    sc = (float)s64;
-                                }
-                            }
+                            if (ok) stage = ys == 0 ? 1 : (ys <= 16 ? 2 : 3);
+                        }
+                    }
+                    if (stage == 2) {
+                        n_verified++;
+                        sc = v + dot_prefix(P.crow + ym.x, ym.z, xtab, RG, xr, xs, xrow, xl);
+                        stage = 1;
+                    }
+                    // long prefixes: the whole warp computes one dot(x, y') at a time
+                    for (unsigned lm = __ballot_sync(0xffffffffu, stage == 3); lm; lm &= lm - 1u) {
+                        const int src = __ffs(lm) - 1;
+                        const int yo = __shfl_sync(0xffffffffu, ym.x, src);
+                        const int yl = __shfl_sync(0xffffffffu, ym.z, src);
+                        float acc = 0.f;
+                        for (int k = lane; k < yl; k += 32) {
+                            const int2 e = P.crow[yo + k];
+                            acc = fmaf(x_at(e.x, xtab, RG, xr, xs, xrow, xl), __int_as_float(e.y), acc);
+                        }
+#pragma unroll
+                        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                        if (lane == src) {
+                            n_verified++;
+                            sc = v + acc;
+                            stage = 1;
+                        }
+                    }
+                    if (stage == 1) {
+                        if (sc >= t + beta) {
+                            emit = true;
+                            stage = 0;
+                        } else if (sc <= t - beta) {
+                            stage = 0;
+                        }
+                    }
+                    // inside the band: float64 dot(x, y) over all of y, one candidate at a
+                    // time across the warp (x's values from shared memory, exact products)
+                    for (unsigned lm = __ballot_sync(0xffffffffu, stage == 1); lm; lm &= lm - 1u) {
+                        const int src = __ffs(lm) - 1;
+                        const int yo = __shfl_sync(0xffffffffu, ym.x, src);
+                        const int yl = __shfl_sync(0xffffffffu, ym.y, src);
+                        double acc = 0.0;
+                        for (int k = lane; k < yl; k += 32) {
+                            const int2 e = P.crow[yo + k];
+                            acc += (double)x_at(e.x, xtab, RG, xr, xs, xrow, xl) * (double)__int_as_float(e.y);
+                        }
+#pragma unroll
+                        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                        if (lane == src) {
+                            n_band++;
+                            emit = acc >= (double)t;
+                            sc = (float)acc;
                         }
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, emit);

@@ -72,7 +72,13 @@ aps_status query_on_stream(aps_index *ix, const int64_t *qptr, const int32_t *qi
     }
     QueryArrays qa;
     APS_TRY(prepare_queries(ix, p, ii, vv, nq, t, flags, s, qa));
-    APS_TRY(join_queries(ix, qa, t, flags, s, out, stats));
+    aps_stats local{};
+    APS_TRY(join_queries(ix, qa, t, flags, s, out, &local));
+    if (stats) *stats = local;
+    {
+        std::lock_guard<std::mutex> lk(ix->stats_mu);
+        ix->stats = local;  // the index reports the counters of its last join or query batch
+    }
     if (flags & APS_HOST_OUTPUT) {
         aps_status st = pairs_to_host(out, s);
         if (st != APS_OK) {
