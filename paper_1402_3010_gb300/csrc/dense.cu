@@ -1,14 +1,17 @@
 // Dense-embedding all-pairs: the matrix view S = D.D^T of the problem definition (Sec. 2.1)
 // on the 5th-generation tensor cores, then exact decisions.
 //
-//   1. X (float32) -> Xb (bfloat16, rows padded with zeros).
-//   2. dense_gemm_kernel: persistent, one CTA per SM. A CTA owns MT x 128 rows of Xb (the
-//      "A" operand, resident in shared memory) and streams 128-row blocks of Xb (the "B"
-//      operand) through a TMA ring. One thread issues tcgen05.mma (128x128x16, BF16 in,
-//      float32 accumulators in tensor memory, double-buffered); eight epilogue warps read
-//      the accumulators with tcgen05.ld and keep (i < j) with S_ij >= t - delta, where
-//      delta bounds |x.y - bf16(x).bf16(y)| plus the float32 accumulation error, so no
-//      pair with x.y >= t is lost.
+//   1. X (float32) -> Xb (bfloat16, rows padded with zeros to a multiple of 256).
+//   2. dense_gemm_kernel: persistent clusters of two CTAs, one CTA per SM. A pair owns a
+//      256-row block of Xb (the "A" operand; each CTA keeps its 128 rows resident in
+//      shared memory) and streams 256-row blocks of Xb (the "B" operand; each CTA loads its
+//      128-row half) through a TMA ring. One thread of the even CTA issues
+//      tcgen05.mma.cta_group::2 (M = N = 256, K = 16, BF16 in, float32 accumulators in the
+//      tensor memory of both SMs, double-buffered); sixteen epilogue warps per CTA read the
+//      accumulators with tcgen05.ld and keep (i < j) with S_ij >= t - delta, where delta
+//      bounds |x.y - bf16(x).bf16(y)| plus the float32 accumulation error, so no pair with
+//      x.y >= t is lost. Sharing B across the pair halves each SM's shared-memory operand
+//      reads per MMA compared with a single-SM 128-row tile.
 //   3. Candidates are sorted by (i, j), rescored in float32 from X (float64 when within
 //      the band of t) and compacted into the result.
 // Every wait on an mbarrier is bounded; on expiry the kernel records an error code and
@@ -27,23 +30,28 @@
 namespace aps {
 namespace {
 
-constexpr int DN_THREADS = 320;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-9: epilogue
-constexpr int EPI_WARPS = 8;     // two per TMEM lane quadrant, each reading half the columns
-constexpr int TILE_ROWS = 128;
-constexpr int KBLK = 64;                   // bf16 elements per 128-byte swizzle row
+constexpr int EPI_WARPS = 16;                     // four per TMEM lane quadrant
+constexpr int DN_THREADS = 64 + 32 * EPI_WARPS;   // warp 0: TMA, warp 1: MMA + TMEM owner, then epilogue
+constexpr int EPI_COLS = 256 / (EPI_WARPS / 4);   // accumulator columns one epilogue warp reads
+constexpr int PAIR_ROWS = 256;                    // rows of an output block (both CTAs)
+constexpr int TILE_ROWS = 128;                    // rows of one CTA's operand tile
+constexpr int KBLK = 64;                          // bf16 elements per 128-byte swizzle row
 constexpr int TILE_BYTES = TILE_ROWS * KBLK * 2;  // 16 KB
 constexpr int SMEM_BUDGET = 224 * 1024;
-constexpr uint32_t TMEM_COLS = 512;
+constexpr int MAX_STAGES = 12;
+constexpr int UNIT_BLOCKS = 32;  // B blocks per work unit
+constexpr uint32_t TMEM_COLS = 512;  // two 256-column accumulators
 constexpr unsigned long long WAIT_LIMIT = 1ull << 26;
 
 struct DenseParams {
-    int n, n_pad, d, KB, MT, S;
+    int n, KB, S;
     int nunits;
-    const int4 *units;  // {super-row block, first B block, end B block, 0}
+    const int4 *units;  // {A block, first B block, end B block, 0}, blocks of 256 rows
     float thr;
     unsigned long long *cand;
     unsigned long long cap;
-    unsigned long long *count;
+    unsigned long long *count;   // candidate slots handed out (reserved in slabs)
+    unsigned long long *padded;  // slots of those left holding CAND_PAD
     int *err;
 };
 
@@ -60,10 +68,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -77,8 +81,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Bounded wait: false (and an error code in *err) when the phase never completes or
-// another role already gave up.
-__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+// another role already gave up. The first probe is inline; the spin is out of line.
+__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, int *err, int code) {
     for (unsigned long long i = 0; i < WAIT_LIMIT; i++) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 4095) == 4095) {
@@ -90,12 +94,8 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err,
     return false;
 }
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-            smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+    return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, err, code);
 }
 
 // Shared-memory matrix descriptor: K-major tile of 128 rows x 128 bytes written by TMA with
@@ -109,25 +109,6 @@ __device__ __forceinline__ uint64_t smem_desc(const void *p) {
     d |= (uint64_t)1 << 46;                // descriptor version
     d |= (uint64_t)2 << 61;                // 128-byte swizzle
     return d;
-}
-
-// Instruction descriptor, kind::f16: BF16 A and B, float32 D, both K-major, M = N = 128.
-__host__ __device__ constexpr uint32_t idesc_bf16_128x128() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -148,17 +129,150 @@ __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t *r) {
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Rare path: record (i, j0 + k) for every set bit k with j > i and j < n.
-__device__ __noinline__ void emit_candidates(unsigned long long mask, int i, int j0, const DenseParams &P) {
+// Largest of 64 values, as a balanced tree (no long dependency chain).
+__device__ __forceinline__ float max64(const uint32_t *r) {
+    float m[32];
+#pragma unroll
+    for (int k = 0; k < 32; k++) m[k] = fmaxf(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
+#pragma unroll
+    for (int w = 16; w; w >>= 1)
+#pragma unroll
+        for (int k = 0; k < w; k++) m[k] = fmaxf(m[k], m[k + w]);
+    return m[0];
+}
+
+__device__ __forceinline__ unsigned long long mask64(const uint32_t *r, float thr) {
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int k = 0; k < 32; k++) {
+        lo |= (__uint_as_float(r[k]) >= thr ? 1u : 0u) << k;
+        hi |= (__uint_as_float(r[k + 32]) >= thr ? 1u : 0u) << k;
+    }
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+constexpr uint32_t EMIT_CHUNK = 256;            // candidate slots a warp reserves at a time
+constexpr unsigned long long CAND_PAD = ~0ull;  // fills reserved slots that stay unused
+
+// A warp's current slice of the candidate list: slots [base + used, base + lim) are its own.
+// Reserving whole slices keeps the shared counter off the per-candidate path.
+struct Slab {
+    unsigned long long base;
+    uint32_t used, lim;
+    unsigned long long padded;  // slots of earlier slices filled with CAND_PAD
+};
+
+// Bits k of a 64-column slice starting at column j0 with i < j0 + k < n.
+__device__ __forceinline__ unsigned long long tri_mask(int i, int j0, int n) {
+    const int lo = max(i - j0 + 1, 0), hi = min(n - j0, 64);
+    if (lo >= hi) return 0ull;
+    const unsigned long long m = hi == 64 ? ~0ull : (1ull << hi) - 1ull;
+    return m & (~0ull << lo);
+}
+
+// Warp-collective: the rest of the current slice becomes padding.
+__device__ __forceinline__ void slab_close(Slab &w, unsigned long long *cand, unsigned long long cap) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t k = w.used + lane; k < w.lim; k += 32)
+        if (w.base + k < cap) cand[w.base + k] = CAND_PAD;
+    w.padded += w.lim - w.used;
+    w.used = w.lim;
+}
+
+// Warp-collective append of the keys i * n + j0 + k, one per set bit k of each lane's mask;
+// lanes are laid out in lane order inside the warp's slice.
+__device__ __forceinline__ void slab_append(Slab &w, unsigned long long mask, int i, int j0, int n,
+                                            unsigned long long *cand, unsigned long long cap,
+                                            unsigned long long *count) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t c = (uint32_t)__popcll(mask);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (w.used + total > w.lim) {
+        slab_close(w, cand, cap);
+        const uint32_t want = max(EMIT_CHUNK, total);
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(count, (unsigned long long)want);
+        w.base = __shfl_sync(0xffffffffu, b, 0);
+        w.used = 0;
+        w.lim = want;
+    }
+    unsigned long long pos = w.base + w.used + (incl - c);
     while (mask) {
         const int k = __ffsll((long long)mask) - 1;
         mask &= mask - 1ull;
-        const int j = j0 + k;
-        if (j > i && j < P.n) {
-            const unsigned long long pos = atomicAdd(P.count, 1ull);
-            if (pos < P.cap) P.cand[pos] = (unsigned long long)i * (unsigned long long)P.n + (unsigned long long)j;
-        }
+        if (pos < cap) cand[pos] = (unsigned long long)i * (unsigned long long)n + (unsigned long long)(j0 + k);
+        pos++;
     }
+    w.used += total;
+}
+
+// Warp-collective, after a warp's last tile: close its slice and count its padding.
+__device__ __forceinline__ void slab_finish(Slab &w, unsigned long long *cand, unsigned long long cap,
+                                            unsigned long long *padded) {
+    slab_close(w, cand, cap);
+    if ((threadIdx.x & 31) == 0 && w.padded) atomicAdd(padded, w.padded);
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t map_to_rank(const void *p, uint32_t rank) {
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(smem_u32(p)), "r"(rank));
+    return out;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Arrive, without release semantics, on a barrier of either CTA of the pair: used where the
+// arrival only says that tensor-memory loads have completed (tcgen05.wait::ld), so no memory
+// writes need to be made visible to the waiter.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar_cluster, int x,
+                                                 int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+        "%4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16_pair(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// arrive on the barrier at this offset in both CTAs of the pair once prior MMAs complete
+__device__ __forceinline__ void umma_commit_pair(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B, float32 D, both K-major, M = N = 256
+// (the pair's shape under cta_group::2).
+__host__ __device__ constexpr uint32_t idesc_bf16_256x256() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
 }
 
 __global__ void __launch_bounds__(DN_THREADS, 1)
@@ -166,15 +280,18 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int MT = P.MT, KB = P.KB, S = P.S;
-    unsigned char *sA = smem;
-    unsigned char *sB = smem + (size_t)MT * KB * TILE_BYTES;
+    const int KB = P.KB, S = P.S;
+    unsigned char *sA = smem;                                  // this CTA's 128 rows of A
+    unsigned char *sB = smem + (size_t)KB * TILE_BYTES;        // this CTA's halves of the B stages
     uint64_t *bars = reinterpret_cast<uint64_t *>(sB + (size_t)S * TILE_BYTES);
     uint64_t *a_full = bars, *a_empty = bars + 1, *done = bars + 2;
     uint64_t *b_full = bars + 3, *b_empty = b_full + S;
     uint64_t *d_full = b_empty + S, *d_empty = d_full + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d_empty + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
 
     if (threadIdx.x == 0) {
         mbar_init(a_full, 1);
@@ -186,41 +303,41 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(&d_full[b], 1);
-            mbar_init(&d_empty[b], EPI_WARPS);
+            mbar_init(&d_empty[b], 2 * EPI_WARPS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(TMEM_COLS)
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     }
-    __syncthreads();
+    cluster_sync_all();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        // ------------------------------------------------------------ TMA producer
+        // ------------------------------------------------------------ TMA producer (both CTAs)
         if (lane == 0) {
+            const uint32_t a_full_l = map_to_rank(a_full, 0);
             int stage = 0;
             uint32_t phase = 0;
             int it = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, it++) {
+            for (int u = cluster; u < P.nunits && ok; u += nclusters, it++) {
                 const int4 U = P.units[u];
                 if (it > 0 && !(ok = mbar_wait(a_empty, (uint32_t)(it - 1) & 1u, P.err, 1))) break;
-                mbar_expect_tx(a_full, (uint32_t)(MT * KB * TILE_BYTES));
-                for (int mt = 0; mt < MT; mt++)
-                    for (int kb = 0; kb < KB; kb++)
-                        tma_load_2d(sA + (size_t)(mt * KB + kb) * TILE_BYTES, &tmap, a_full, kb * KBLK,
-                                    (U.x * MT + mt) * TILE_ROWS);
+                if (leader) mbar_expect_tx(a_full, (uint32_t)(2 * KB * TILE_BYTES));
+                for (int kb = 0; kb < KB; kb++)
+                    tma_load_2d_pair(sA + (size_t)kb * TILE_BYTES, &tmap, a_full_l, kb * KBLK,
+                                     U.x * PAIR_ROWS + (int)rank * TILE_ROWS);
                 for (int bc = U.y; bc < U.z && ok; bc++) {
                     for (int kb = 0; kb < KB; kb++) {
                         if (!(ok = mbar_wait(&b_empty[stage], phase ^ 1u, P.err, 2))) break;
-                        mbar_expect_tx(&b_full[stage], (uint32_t)TILE_BYTES);
-                        tma_load_2d(sB + (size_t)stage * TILE_BYTES, &tmap, &b_full[stage], kb * KBLK,
-                                    bc * TILE_ROWS);
+                        if (leader) mbar_expect_tx(&b_full[stage], (uint32_t)(2 * TILE_BYTES));
+                        tma_load_2d_pair(sB + (size_t)stage * TILE_BYTES, &tmap, map_to_rank(&b_full[stage], 0),
+                                         kb * KBLK, bc * PAIR_ROWS + (int)rank * TILE_ROWS);
                         if (++stage == S) {
                             stage = 0;
                             phase ^= 1u;
@@ -230,10 +347,9 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
             }
         }
     } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_128x128();
-            // descriptors of the first A tile and the first B stage; tiles are 16 KB apart
+        // ------------------------------------------------------------ MMA issuer (even CTA)
+        if (lane == 0 && leader) {
+            const uint32_t idesc = idesc_bf16_256x256();
             const uint64_t adesc0 = smem_desc(sA), bdesc0 = smem_desc(sB);
             int stage = 0;
             uint32_t phase = 0;
@@ -241,84 +357,76 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
             uint32_t uses[2] = {0, 0};
             int it = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, it++) {
+            for (int u = cluster; u < P.nunits && ok; u += nclusters, it++) {
                 const int4 U = P.units[u];
                 if (!(ok = mbar_wait(a_full, (uint32_t)it & 1u, P.err, 3))) break;
-                tc_fence_after();
                 for (int bc = U.y; bc < U.z && ok; bc++) {
                     if (!(ok = mbar_wait(&d_empty[buf], (uses[buf] & 1u) ^ 1u, P.err, 4))) break;
                     tc_fence_after();
+                    const uint32_t td = tmem + (uint32_t)(buf * 256);
                     for (int kb = 0; kb < KB; kb++) {
                         if (!(ok = mbar_wait(&b_full[stage], phase, P.err, 5))) break;
-                        tc_fence_after();
                         const uint64_t bdesc = bdesc0 + (uint64_t)(stage * (TILE_BYTES >> 4));
                         const uint64_t adesc = adesc0 + (uint64_t)(kb * (TILE_BYTES >> 4));
-                        const uint32_t td = tmem + (uint32_t)(buf * 256);
 #pragma unroll
-                        for (int k16 = 0; k16 < KBLK / 16; k16++) {
-                            umma_bf16(td, adesc + 2u * k16, bdesc + 2u * k16, idesc, (kb | k16) != 0);
-                            if (MT == 2)
-                                umma_bf16(td + 128u, adesc + (uint64_t)(KB * (TILE_BYTES >> 4)) + 2u * k16,
-                                          bdesc + 2u * k16, idesc, (kb | k16) != 0);
-                        }
-                        umma_commit(&b_empty[stage]);  // the stage is free once these MMAs finish
+                        for (int k16 = 0; k16 < KBLK / 16; k16++)
+                            umma_bf16_pair(td, adesc + 2u * k16, bdesc + 2u * k16, idesc, (kb | k16) != 0);
+                        umma_commit_pair(&b_empty[stage]);  // frees the stage in both CTAs
                         if (++stage == S) {
                             stage = 0;
                             phase ^= 1u;
                         }
                     }
                     if (!ok) break;
-                    umma_commit(&d_full[buf]);
+                    umma_commit_pair(&d_full[buf]);
                     uses[buf]++;
                     buf ^= 1;
                 }
-                umma_commit(a_empty);
+                umma_commit_pair(a_empty);
             }
-            // every MMA issued by this thread has completed before TMEM is released
-            umma_commit(done);
+            umma_commit_pair(done);
             mbar_wait(done, 0, P.err, 6);
         }
     } else {
-        // ------------------------------------------------------------ epilogue
-        const int q = warp & 3;           // TMEM lane quadrant this warp may read
-        const int h = (warp - 2) >> 2;    // which 64-column half of each accumulator
+        // ------------------------------------------------------------ epilogue (both CTAs)
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;  // which EPI_COLS-column slice of the 256 columns
         int buf = 0;
         uint32_t uses[2] = {0, 0};
         bool ok = true;
-        for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
+        Slab w = {0ull, 0u, 0u, 0ull};
+        for (int u = cluster; u < P.nunits && ok; u += nclusters) {
             const int4 U = P.units[u];
+            const int i = U.x * PAIR_ROWS + (int)rank * TILE_ROWS + q * 32 + lane;
             for (int bc = U.y; bc < U.z; bc++) {
-                if (!(ok = mbar_wait(&d_full[buf], uses[buf] & 1u, P.err, 7))) break;
+                if (!(ok = __all_sync(0xffffffffu, mbar_wait(&d_full[buf], uses[buf] & 1u, P.err, 7)))) break;
                 tc_fence_after();
-                for (int mt = 0; mt < MT; mt++) {
-                    const int i = (U.x * MT + mt) * TILE_ROWS + q * 32 + lane;
-                    const uint32_t col = (uint32_t)(buf * 256 + mt * 128 + h * 64);
-                    uint32_t r[64];
-                    tmem_ld32_issue(tmem + ((uint32_t)(q * 32) << 16) + col, r);
-                    tmem_ld32_issue(tmem + ((uint32_t)(q * 32) << 16) + col + 32, r + 32);
-                    tmem_ld_wait();
-                    // bit k: column k of this half reaches the candidate threshold
-                    uint32_t lo = 0, hi = 0;
+                uint32_t r[EPI_COLS];
+                const uint32_t col = (uint32_t)(buf * 256 + h * EPI_COLS);
 #pragma unroll
-                    for (int k = 0; k < 32; k++) {
-                        lo |= (__uint_as_float(r[k]) >= P.thr ? 1u : 0u) << k;
-                        hi |= (__uint_as_float(r[k + 32]) >= P.thr ? 1u : 0u) << k;
-                    }
-                    unsigned long long mask = ((unsigned long long)hi << 32) | lo;
-                    if (mask != 0ull && i < P.n) emit_candidates(mask, i, bc * TILE_ROWS + h * 64, P);
-                }
+                for (int cc = 0; cc < EPI_COLS / 32; cc++)
+                    tmem_ld32_issue(tmem + ((uint32_t)(q * 32) << 16) + col + 32 * cc, r + 32 * cc);
+                tmem_ld_wait();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&d_empty[buf]);
+                if (lane == 0) mbar_arrive_cluster(map_to_rank(&d_empty[buf], 0));
+                for (int cc = 0; cc < EPI_COLS / 64; cc++) {
+                    const int j0 = bc * PAIR_ROWS + h * EPI_COLS + cc * 64;
+                    unsigned long long m = 0ull;
+                    if (max64(r + 64 * cc) >= P.thr && i < P.n) m = mask64(r + 64 * cc, P.thr) & tri_mask(i, j0, P.n);
+                    if (__any_sync(0xffffffffu, m != 0ull)) slab_append(w, m, i, j0, P.n, P.cand, P.cap, P.count);
+                }
                 uses[buf]++;
                 buf ^= 1;
             }
         }
+        slab_finish(w, P.cand, P.cap, P.padded);
     }
     __syncthreads();
+    cluster_sync_all();  // the peer no longer touches this CTA's barriers or tensor memory
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
 
@@ -454,13 +562,10 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
         set_error("the dense path needs an sm_103 device (found sm_%d%d)", major, minor);
         return APS_EUNSUPPORTED;
     }
-    const int MT = d <= 256 ? 2 : 1;
     const int KB = d / KBLK;
-    const int64_t blk = (int64_t)TILE_ROWS * MT;
-    const int64_t n_pad = std::max<int64_t>(blk, ((int64_t)n + blk - 1) / blk * blk);
-    const int abytes = MT * KB * TILE_BYTES;
-    const int S = std::min(8, (SMEM_BUDGET - abytes) / TILE_BYTES);
-    const int smem = abytes + S * TILE_BYTES + 1024 + 512;
+    const int64_t n_pad = std::max<int64_t>(PAIR_ROWS, ((int64_t)n + PAIR_ROWS - 1) / PAIR_ROWS * PAIR_ROWS);
+    const int S = std::min(MAX_STAGES, (SMEM_BUDGET - KB * TILE_BYTES) / TILE_BYTES);
+    const int smem = (KB + S) * TILE_BYTES + 1024 + 512;  // operands, alignment slack, barriers
     cudaEvent_t ev[5];
     for (int i = 0; i < 5; i++) APS_CUDA(cudaEventCreate(&ev[i]));
     struct EvGuard {
@@ -476,13 +581,12 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
     APS_LAUNCH_CHECK();
     CUtensorMap map;
     APS_TRY(encode_map(&map, Xb.p, n_pad, d));
-    // work units: (super-row block, run of B blocks), B blocks from the diagonal onward
-    const int64_t nsr = n_pad / blk, nb = n_pad / TILE_ROWS;
-    const int L = 64;
+    // work units: (A block, run of B blocks), B blocks from the diagonal onward
+    const int64_t nb = n_pad / PAIR_ROWS;
     std::vector<int4> units;
-    for (int64_t sr = 0; sr < nsr; sr++)
-        for (int64_t b = sr * MT; b < nb; b += L)
-            units.push_back(make_int4((int)sr, (int)b, (int)std::min<int64_t>(b + L, nb), 0));
+    for (int64_t a = 0; a < nb; a++)
+        for (int64_t b = a; b < nb; b += UNIT_BLOCKS)
+            units.push_back(make_int4((int)a, (int)b, (int)std::min<int64_t>(b + UNIT_BLOCKS, nb), 0));
     DBuf<int4> dunits;
     APS_TRY(dunits.alloc(units.size(), s));
     APS_CUDA(cudaMemcpyAsync(dunits.p, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, s));
@@ -490,11 +594,32 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
     DBuf<int> err;
     APS_TRY(ctr.alloc(4, s));
     APS_TRY(err.alloc(1, s));
-    APS_CUDA(cudaFuncSetAttribute(dense_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    constexpr int SMEM_MAX = SMEM_BUDGET + 1024 + 512;
+    APS_CUDA(cudaFuncSetAttribute(dense_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX));
     const double delta = dense_margin(d);
+    // one cluster per SM pair that can be resident at once
+    static int max_clusters = 0;
+    if (!max_clusters) {
+        cudaLaunchConfig_t q;
+        memset(&q, 0, sizeof(q));
+        q.gridDim = dim3((unsigned)(num_sms() & ~1));
+        q.blockDim = dim3(DN_THREADS);
+        q.dynamicSmemBytes = (size_t)SMEM_MAX;
+        cudaLaunchAttribute qa[1];
+        qa[0].id = cudaLaunchAttributeClusterDimension;
+        qa[0].val.clusterDim.x = 2;
+        qa[0].val.clusterDim.y = 1;
+        qa[0].val.clusterDim.z = 1;
+        q.attrs = qa;
+        q.numAttrs = 1;
+        int c = 0;
+        APS_CUDA(cudaOccupancyMaxActiveClusters(&c, dense_gemm_kernel, &q));
+        max_clusters = std::max(1, c);
+    }
+    const int npairs_sm = std::max(1, std::min<int>(max_clusters, (int)units.size()));
     int64_t cap = std::max<int64_t>({g_dense_hint.load(), (int64_t)1 << 22, (int64_t)n * 4});
     DBuf<unsigned long long> cand;
-    int64_t nc = 0;
+    int64_t nslots = 0, npad = 0;
     float ms_gemm = 0.f;
     for (int attempt = 0; attempt < 2; attempt++) {
         APS_TRY(cand.alloc((size_t)cap, s));
@@ -502,10 +627,7 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
         APS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
         DenseParams P;
         P.n = n;
-        P.n_pad = (int)n_pad;
-        P.d = d;
         P.KB = KB;
-        P.MT = MT;
         P.S = S;
         P.nunits = (int)units.size();
         P.units = dunits.p;
@@ -513,15 +635,28 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
         P.cand = cand.p;
         P.cap = (unsigned long long)cap;
         P.count = ctr.p;
+        P.padded = ctr.p + 2;
         P.err = err.p;
-        const int grid = std::max(1, std::min<int>(num_sms(), P.nunits));
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3((unsigned)(2 * npairs_sm));
+        cfg.blockDim = dim3(DN_THREADS);
+        cfg.dynamicSmemBytes = (size_t)smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
         APS_CUDA(cudaEventRecord(ev[1], s));
-        dense_gemm_kernel<<<grid, DN_THREADS, smem, s>>>(map, P);
-        APS_LAUNCH_CHECK();
+        APS_CUDA(cudaLaunchKernelEx(&cfg, dense_gemm_kernel, map, P));
+        count_launch();
         APS_CUDA(cudaEventRecord(ev[2], s));
-        unsigned long long cnt = 0;
+        unsigned long long cnt[3] = {0, 0, 0};
         int e_h = 0;
-        APS_CUDA(cudaMemcpyAsync(&cnt, ctr.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+        APS_CUDA(cudaMemcpyAsync(cnt, ctr.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
         APS_CUDA(cudaMemcpyAsync(&e_h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         APS_CUDA(cudaStreamSynchronize(s));
         if (e_h) {
@@ -529,19 +664,21 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
             return APS_ETIMEOUT;
         }
         cudaEventElapsedTime(&ms_gemm, ev[1], ev[2]);
-        nc = (int64_t)cnt;
-        if (nc <= cap) break;
-        cap = nc + nc / 8 + 1024;
+        nslots = (int64_t)cnt[0];
+        npad = (int64_t)cnt[2];
+        if (nslots <= cap) break;
+        cap = nslots + nslots / 8 + 1024;
     }
-    g_dense_hint.store(nc + nc / 8 + 1024);
-    // sort candidates by (i, j), rescore, compact
+    g_dense_hint.store(nslots + nslots / 8 + 1024);
+    // sort by (i, j): the slots hold nc candidates and npad CAND_PAD keys, which sort last
     DBuf<uint32_t> dummy;
-    APS_TRY(dummy.alloc((size_t)std::max<int64_t>(nc, 1), s));
-    if (nc > 1) {
-        APS_CUDA(cudaMemsetAsync(dummy.p, 0, sizeof(uint32_t) * nc, s));
-        APS_TRY(sort_pairs(reinterpret_cast<uint64_t *>(cand.p), dummy.p, nc,
+    APS_TRY(dummy.alloc((size_t)std::max<int64_t>(nslots, 1), s));
+    if (nslots > 1) {
+        APS_CUDA(cudaMemsetAsync(dummy.p, 0, sizeof(uint32_t) * nslots, s));
+        APS_TRY(sort_pairs(reinterpret_cast<uint64_t *>(cand.p), dummy.p, nslots,
                            bits_for((uint64_t)n * (uint64_t)n), s));
     }
+    const int64_t nc = nslots - npad;
     APS_CUDA(cudaEventRecord(ev[3], s));
     DBuf<int32_t> keep;
     DBuf<float> sc;

@@ -39,7 +39,8 @@ def run_dense(aps, X, t, flags=0, device=True):
     return i, j, s, st
 
 
-@pytest.mark.parametrize("n,d,k", [(700, 128, 20), (3001, 256, 60), (1500, 64, 30), (1200, 512, 25), (129, 192, 5)])
+@pytest.mark.parametrize("n,d,k", [(700, 128, 20), (3001, 256, 60), (1500, 64, 30), (1200, 512, 25), (129, 192, 5),
+                                   (1100, 512, 25), (257, 384, 6), (5000, 320, 80)])
 def test_dense_mixture_full_parity(aps, n, d, k):
     X = synth.dense_mixture(n, d, k, 0.15, seed=n + d)
     t = 0.8
