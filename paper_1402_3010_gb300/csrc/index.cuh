@@ -29,7 +29,6 @@ namespace aps {
 constexpr int JOIN_THREADS = 1024;
 constexpr int JOIN_WMAX = 40960;  // accumulator slots of a whole CTA (160 KB)
 constexpr int JOIN_RMAX = 2048;   // dense rank table for dot(x, y') lookups (8 KB)
-constexpr int JOIN_RING = 128;    // per-warp ring of candidate slots awaiting verification
 constexpr int JOIN_XCAP = 2048;   // x's row kept in shared memory when |x| <= XCAP / G
 // per-warp list of emitted pairs of one window: a warp scans at most W/NW slots rounded
 // up to 128 (W/NW = 1280 for every group shape)

@@ -75,7 +75,7 @@ __host__ __device__ constexpr int group_bytes(int G) {
            + 4 * (JOIN_THREADS / G + 4)              // c_ch0
            + 4 * (JOIN_THREADS / G)                  // c_xv
            + 4 * (JOIN_RMAX / G)                     // xtab
-           + 4 * JOIN_RING * (NWARPS / G)            // candidate rings
+           + 4 * (JOIN_WMAX / G / 32)                // touched-slot bitmap
            + 8 * (JOIN_XCAP / G)                     // x's row
            + 8 * 32                                  // wsum
            + 4 * 32                                  // wcnt
@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     int32_t *c_ch0 = c_cnt + GT;                                    // [GT + 4] chunk prefix
     float *c_xv = reinterpret_cast<float *>(c_ch0 + GT + 4);        // [GT]
     float *xtab = c_xv + GT;                                        // [RG]
-    int32_t *ring = reinterpret_cast<int32_t *>(xtab + RG) + gw * JOIN_RING;
-    int2 *xr = reinterpret_cast<int2 *>(reinterpret_cast<int32_t *>(xtab + RG) + JOIN_RING * NW);
+    uint32_t *bm = reinterpret_cast<uint32_t *>(xtab + RG);        // [WG / 32]
+    int2 *xr = reinterpret_cast<int2 *>(bm + WG / 32);
     const int XG = JOIN_XCAP / G;
     int64_t *wsum = reinterpret_cast<int64_t *>(xr + XG);
     int32_t *wcnt = reinterpret_cast<int32_t *>(wsum + 32);
@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     const bool f_upper = !(P.flags & APS_NO_UPPERBOUND);
 
     for (int i = gt; i < WG; i += GT) A[i] = 0.f;
+    for (int i = gt; i < WG / 32; i += GT) bm[i] = 0u;
     unsigned long long n_visits = 0, n_cand = 0, n_verified = 0, n_band = 0, n_pairs = 0;
 
     for (;;) {
@@ -321,6 +322,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                             const float prod = cxv * __int_as_float(ent[u].y);
                             if (phase == 0) {
                                 atomicAdd(&A[slot], prod);
+                                atomicOr(&bm[slot >> 5], 1u << (slot & 31));
                             } else if (A[slot] != 0.f) {
                                 atomicAdd(&A[slot], prod);
                             }
@@ -330,42 +332,45 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                 gsync(G, g, GT);
             }
             if (!created) continue;  // no candidate can exist in this window
-            // ---------------- verify. Slots are read 2 at a time from an even start;
-            // slots below lo or past wn are zero (never accumulated into). Candidates are
-            // compacted into a per-warp ring, verified 32 at a time, cleared from A, and
-            // the emitted (y, score) go to the warp's scratch list in increasing y.
-            const int lo2 = lo & ~1;
-            const int wn2 = (wn + 1) & ~1;
-            const int span = wn2 - lo2;
-            const int chunk = span > 0 ? (((span + NW - 1) / NW + 63) & ~63) : 0;
-            const int sb0 = lo2 + gw * chunk;
-            const int se = min(lo2 + (gw + 1) * chunk, wn2);
+            // ---------------- verify. The creating pass set one bit of bm per touched slot.
+            // Each warp walks its share of bm 32 words (1024 slots) at a time and takes the
+            // set bits in slot order, 32 candidates per batch: lane j of a batch takes the
+            // candidate at position b + j, located from the lanes' popcount prefix. Taken
+            // slots are cleared in A (bm words as they are read), and the emitted (y, score)
+            // go to the warp's scratch list in increasing y.
+            const int wlo = lo >> 5, whi = (wn + 31) >> 5;
+            const int wper = (whi - wlo + NW - 1) / NW;
+            const int wb = wlo + gw * wper, we = min(wb + wper, whi);
             int ne = 0;
-            int head = 0, tail = 0;  // warp-uniform ring cursors
-            for (int sb = sb0; sb < se || tail > head; sb += 64) {
-                if (sb < se) {  // append this 64-slot block's candidates to the ring
-                    const int s2 = sb + lane * 2;
-                    float2 v2 = make_float2(0.f, 0.f);
-                    if (s2 < se) v2 = *reinterpret_cast<const float2 *>(&A[s2]);
-                    const int cnt = (v2.x != 0.f) + (v2.y != 0.f);
-                    int tot;
-                    int pos = tail + warp_excl_scan_int(cnt, lane, &tot);
-                    if (v2.x != 0.f) ring[(pos++) & (JOIN_RING - 1)] = s2;
-                    if (v2.y != 0.f) ring[(pos++) & (JOIN_RING - 1)] = s2 + 1;
-                    tail += tot;
-                    __syncwarp();
+            for (int wq = wb; wq < we; wq += 32) {
+                uint32_t word = 0u;
+                if (wq + lane < we) {
+                    word = bm[wq + lane];
+                    bm[wq + lane] = 0u;
                 }
-                // verify full batches of 32 (and the rest once the scan is done)
-                while (tail - head >= 32 || (sb + 64 >= se && tail > head)) {
-                    const int nb = min(32, tail - head);
+                const int c = __popc(word);
+                int T;
+                const int excl = warp_excl_scan_int(c, lane, &T);
+                const int incl = excl + c;
+                for (int b0 = 0; b0 < T; b0 += 32) {
+                    const int p = b0 + lane;
+                    // owner: the first lane whose inclusive count exceeds p (31 when p >= T)
+                    int own = 0;
+#pragma unroll
+                    for (int step = 16; step; step >>= 1)
+                        if (__shfl_sync(0xffffffffu, incl, own + step - 1) <= p) own += step;
+                    uint32_t ow = __shfl_sync(0xffffffffu, word, own);
+                    const int oex = __shfl_sync(0xffffffffu, excl, own);
+                    const bool have = p < T;
                     bool emit = false;
                     float sc = 0.f, v = 0.f;
                     int s = 0;
                     int4 ym = make_int4(0, 0, 0, 0);
                     // 0: rejected, 1: score known, 2: short dot(x, y') left, 3: long dot left
                     int stage = 0;
-                    if (lane < nb) {
-                        s = ring[(head + lane) & (JOIN_RING - 1)];
+                    if (have) {
+                        for (int k = p - oex; k > 0; k--) ow &= ow - 1u;
+                        s = ((wq + own) << 5) + (__ffs(ow) - 1);
                         v = A[s];
                         A[s] = 0.f;
                         const int64_t gy = I.vbase + w0 + s;
@@ -433,9 +438,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     const unsigned bal = __ballot_sync(0xffffffffu, emit);
                     if (emit) elist[ne + __popc(bal & lt_mask)] = make_int2(w0 + s, __float_as_int(sc));
                     ne += __popc(bal);
-                    n_cand += (lane < nb) ? 1ull : 0ull;
-                    head += nb;
-                    __syncwarp();  // ring slots just read may be refilled by any lane next
+                    n_cand += have ? 1ull : 0ull;
                 }
             }
             if (lane == 0) wcnt[gw] = ne;
