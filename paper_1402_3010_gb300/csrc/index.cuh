@@ -33,6 +33,7 @@ constexpr int JOIN_XCAP = 2048;   // x's row kept in shared memory when |x| <= X
 // per-warp list of emitted pairs of one window: a warp scans at most W/NW slots rounded
 // up to 128 (W/NW = 1280 for every group shape)
 constexpr int JOIN_ECAP = JOIN_WMAX / (JOIN_THREADS / 32) + 128;
+constexpr int JOIN_STAGE_SLAB = 4096;  // staging slots a query group reserves at a time
 
 struct InstDesc {
     int64_t vbase;   // first global vector id
@@ -49,10 +50,9 @@ struct InstDesc {
     int32_t packed;  // 1: posting ids carry the size class in their top byte
 };
 
-struct Segment {      // one contiguous run of emitted pairs of one (x, window)
+struct Segment {      // the run of emitted pairs of one (x, window) slot qw, stored at segs[qw]
     int64_t src;      // offset in the staging buffer
-    int64_t qw;       // (vector, window) slot: destination = scan(counts)[qw]
-    int32_t cnt;      // pairs
+    int32_t cnt;      // pairs (also in the per-slot counts; destination = scan(counts)[qw])
     int32_t i;        // local id of x
 };
 
@@ -110,7 +110,6 @@ struct aps_index {
     int64_t class_begin[5] = {0, 0, 0, 0, 0};  // classes G = 1, 2, 4, 8
     // output sizing from the previous join
     int64_t hint_pairs = 0;
-    int64_t hint_segs = 0;
     aps_stats stats{};
     std::mutex stats_mu;  // queries may run concurrently (serving slots)
 };

@@ -49,10 +49,9 @@ struct JoinParams {
     uint32_t flags;
     int2 *stage;
     int64_t stage_cap;
-    unsigned long long *stage_count;
-    Segment *segs;
-    int64_t seg_cap;
-    unsigned long long *seg_count;
+    unsigned long long *stage_count;  // staging slots handed out (in slabs of stage_slab)
+    int64_t stage_slab;
+    Segment *segs;                    // [slots]: the run of slot qw
     int32_t *cntq;
     unsigned long long *counters;  // visits, candidates, verified, pairs, band
     unsigned long long *work;
@@ -79,7 +78,7 @@ __host__ __device__ constexpr int group_bytes(int G) {
            + 8 * (JOIN_XCAP / G)                     // x's row
            + 8 * 32                                  // wsum
            + 4 * 32                                  // wcnt
-           + 8 * 4;                                  // broadcast
+           + 8 * 8;                                  // broadcast and the staging slab
 }
 
 __device__ __forceinline__ void gsync(int G, int g, int GT) {
@@ -184,6 +183,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
 
     for (int i = gt; i < WG; i += GT) A[i] = 0.f;
     for (int i = gt; i < WG / 32; i += GT) bm[i] = 0u;
+    if (gt == 0) bc[3] = bc[4] = bc[5] = 0;  // this group's staging slab: base, used, size
     unsigned long long n_visits = 0, n_cand = 0, n_verified = 0, n_band = 0, n_pairs = 0;
 
     for (;;) {
@@ -443,32 +443,37 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
             }
             if (lane == 0) wcnt[gw] = ne;
             gsync(G, g, GT);
-            if (gt == 0) {
-                int64_t tot = 0;
-                for (int k = 0; k < NW; k++) {
-                    const int c = wcnt[k];
-                    wcnt[k] = (int32_t)tot;
-                    tot += c;
-                }
-                const int64_t qw = P.qmode ? x * I.nw + w : I.qwbase + (int64_t)lx * I.nw + w;
-                P.cntq[qw] = (int32_t)tot;
-                int64_t b = 0, wr = 0;
-                if (tot > 0) {
-                    b = (int64_t)atomicAdd(P.stage_count, (unsigned long long)tot);
-                    const int64_t sid = (int64_t)atomicAdd(P.seg_count, 1ull);
-                    if (b + tot <= P.stage_cap && sid < P.seg_cap) {
-                        Segment S;
-                        S.src = b;
-                        S.qw = qw;
-                        S.cnt = (int32_t)tot;
-                        S.i = P.qmode ? (int32_t)x : lx;
-                        P.segs[sid] = S;
-                        wr = 1;
+            if (gw == 0) {  // offsets of the warps' runs; the window's run in the group's slab
+                const int cw = lane < NW ? wcnt[lane] : 0;
+                int tot;
+                const int exw = warp_excl_scan_int(cw, lane, &tot);
+                if (lane < NW) wcnt[lane] = exw;
+                if (lane == 0) {
+                    const int64_t qw = P.qmode ? x * I.nw + w : I.qwbase + (int64_t)lx * I.nw + w;
+                    P.cntq[qw] = tot;
+                    int64_t b = 0, wr = 0;
+                    if (tot > 0) {
+                        if (bc[4] + tot > bc[5]) {  // a new slab: one global atomic per slab
+                            const int64_t want = max(P.stage_slab, (int64_t)tot);
+                            bc[3] = (int64_t)atomicAdd(P.stage_count, (unsigned long long)want);
+                            bc[4] = 0;
+                            bc[5] = want;
+                        }
+                        b = bc[3] + bc[4];
+                        bc[4] += tot;
+                        if (b + tot <= P.stage_cap) {
+                            Segment S;
+                            S.src = b;
+                            S.cnt = tot;
+                            S.i = P.qmode ? (int32_t)x : lx;
+                            P.segs[qw] = S;
+                            wr = 1;
+                        }
                     }
+                    n_pairs += (unsigned long long)tot;
+                    bc[1] = b;
+                    bc[2] = wr;
                 }
-                n_pairs += (unsigned long long)tot;
-                bc[1] = b;
-                bc[2] = wr;
             }
             gsync(G, g, GT);
             // ---------------- copy the warp's emitted pairs to the reserved run
@@ -489,13 +494,18 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     }
 }
 
-__global__ void k_gather(const Segment *__restrict__ segs, int64_t nseg, const int2 *__restrict__ stage,
-                         const int64_t *__restrict__ qwoff, int32_t *__restrict__ oi, int32_t *__restrict__ oj,
-                         float *__restrict__ os) {
-    for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
-        const Segment S = segs[sg];
-        const int64_t dst = qwoff[S.qw];
-        for (int e = threadIdx.x; e < S.cnt; e += blockDim.x) {
+// One warp per (x, window) slot: copy its staged run to the output at scan(counts)[qw].
+__global__ void k_gather(const Segment *__restrict__ segs, const int32_t *__restrict__ cntq, int64_t nqw,
+                         const int2 *__restrict__ stage, const int64_t *__restrict__ qwoff, int32_t *__restrict__ oi,
+                         int32_t *__restrict__ oj, float *__restrict__ os) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nqw; q += nwarps) {
+        const int cnt = cntq[q];
+        if (cnt == 0) continue;
+        const Segment S = segs[q];
+        const int64_t dst = qwoff[q];
+        for (int e = lane; e < cnt; e += 32) {
             const int2 v = stage[S.src + e];
             oi[dst + e] = S.i;
             oj[dst + e] = v.x;
@@ -535,20 +545,19 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     APS_TRY(cntq.alloc((size_t)std::max<int64_t>(ix->nqw, 1), s));
     APS_TRY(ctr.alloc(16, s));
     // Staging capacity: the index's own hint, else the last join of this process; a join
-    // that still overflows is re-run once with the exact size. At most one segment per
-    // (vector, window) slot exists, so the segment table never overflows.
+    // that still overflows is re-run with room for what it reserved plus one slab per
+    // group. Segments are stored per (vector, window) slot, so their table never overflows.
     int64_t stage_cap = std::max<int64_t>({ix->hint_pairs, g_stage_hint.load(), (int64_t)1 << 20, ix->nnz});
-    int64_t seg_cap = std::max<int64_t>(ix->nqw, 1);
     DBuf<int2> stage;
     DBuf<Segment> segs;
     DBuf<int2> scratch;
     APS_TRY(scratch.alloc((size_t)sms * NWARPS * JOIN_ECAP, s));
-    int64_t total_pairs = 0, total_segs = 0;
+    APS_TRY(segs.alloc((size_t)std::max<int64_t>(ix->nqw, 1), s));
+    int64_t total_pairs = 0, reserved = 0;
     unsigned long long ch[16];
     int reruns = 0;
     for (int attempt = 0; attempt < 3; attempt++) {
         APS_TRY(stage.alloc((size_t)stage_cap, s));
-        APS_TRY(segs.alloc((size_t)seg_cap, s));
         APS_CUDA(cudaMemsetAsync(ctr.p, 0, 16 * sizeof(unsigned long long), s));
         if (ix->nqw) APS_CUDA(cudaMemsetAsync(cntq.p, 0, sizeof(int32_t) * ix->nqw, s));
         APS_CUDA(cudaEventRecord(ev[0], s));
@@ -574,9 +583,8 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
             P.stage = stage.p;
             P.stage_cap = stage_cap;
             P.stage_count = ctr.p + 5;
+            P.stage_slab = JOIN_STAGE_SLAB;
             P.segs = segs.p;
-            P.seg_cap = seg_cap;
-            P.seg_count = ctr.p + 6;
             P.cntq = cntq.p;
             P.counters = ctr.p;
             P.work = ctr.p + 8 + c;
@@ -591,20 +599,18 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
         APS_CUDA(cudaEventRecord(ev[1], s));
         APS_CUDA(cudaMemcpyAsync(ch, ctr.p, sizeof(ch), cudaMemcpyDeviceToHost, s));
         APS_CUDA(cudaStreamSynchronize(s));
-        total_pairs = (int64_t)ch[5];
-        total_segs = (int64_t)ch[6];
-        if (total_pairs <= stage_cap && total_segs <= seg_cap) break;
-        // the staging buffers were too small: grow to the exact need and run again
+        total_pairs = (int64_t)ch[3];
+        reserved = (int64_t)ch[5];
+        if (reserved <= stage_cap) break;
+        // the staging buffer was too small: grow it and run again
         reruns++;
-        stage_cap = std::max<int64_t>(total_pairs, 1);
-        seg_cap = std::max<int64_t>(total_segs, 1);
+        stage_cap = reserved + (int64_t)sms * 8 * JOIN_STAGE_SLAB;  // plus one slab per group
         if (attempt == 2) {
             set_error("pair staging overflow persisted");
             return APS_EOVERFLOW;
         }
     }
-    ix->hint_pairs = total_pairs + total_pairs / 16 + 1024;
-    ix->hint_segs = total_segs + total_segs / 16 + 1024;
+    ix->hint_pairs = reserved + reserved / 16 + 1024;
     g_stage_hint.store(ix->hint_pairs);
     APS_CUDA(cudaEventRecord(ev[3], s));
 
@@ -625,9 +631,9 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     int32_t *oi = reinterpret_cast<int32_t *>(blk);
     int32_t *oj = reinterpret_cast<int32_t *>(blk + (((size_t)npairs * 4 + 127) & ~(size_t)127));
     float *os = reinterpret_cast<float *>(blk + 2 * (((size_t)npairs * 4 + 127) & ~(size_t)127));
-    if (total_segs > 0) {
-        const unsigned grid = (unsigned)std::min<int64_t>(total_segs, (int64_t)sms * 32);
-        k_gather<<<grid, 256, 0, s>>>(segs.p, total_segs, stage.p, qwoff.p, oi, oj, os);
+    if (npairs > 0) {
+        k_gather<<<grid_for(ix->nqw * 32, 256, (int64_t)sms * 32), 256, 0, s>>>(segs.p, cntq.p, ix->nqw, stage.p,
+                                                                               qwoff.p, oi, oj, os);
         APS_LAUNCH_CHECK();
     }
     if (pair_offsets_h) {
@@ -815,9 +821,8 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
         P.stage = stage;
         P.stage_cap = stage_cap;
         P.stage_count = ctr + 5;
+        P.stage_slab = 256;  // small slabs: the arena's staging room is modest
         P.segs = segs;
-        P.seg_cap = nqw;
-        P.seg_count = ctr + 6;
         P.cntq = cntq;
         P.counters = ctr;
         P.work = ctr + 8 + c;
@@ -831,10 +836,11 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
     unsigned long long ch[16];
     APS_CUDA(cudaMemcpyAsync(ch, ctr, sizeof(ch), cudaMemcpyDeviceToHost, s));
     APS_CUDA(cudaStreamSynchronize(s));
-    const int64_t total = (int64_t)ch[5];
+    const int64_t total = (int64_t)ch[3];
     *count = total;
-    if (total > stage_cap) {
-        set_error("%lld pairs exceed the arena's staging room of %lld pairs", (long long)total, (long long)stage_cap);
+    if ((int64_t)ch[5] > stage_cap) {
+        set_error("%lld staged pairs (%lld emitted) exceed the arena's staging room of %lld pairs",
+                  (long long)ch[5], (long long)total, (long long)stage_cap);
         return APS_EOVERFLOW;
     }
     if (total > cap) {
@@ -843,10 +849,9 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
     }
     k_scan_single<<<1, SCAN1_THREADS, 0, s>>>(cntq, ix->nqw, qwoff);
     APS_LAUNCH_CHECK();
-    const int64_t nseg = (int64_t)ch[6];
-    if (nseg > 0) {
-        k_gather<<<(unsigned)std::min<int64_t>(nseg, (int64_t)num_sms() * 32), 256, 0, s>>>(segs, nseg, stage, qwoff,
-                                                                                            oi, oj, os);
+    if (total > 0) {
+        k_gather<<<grid_for(ix->nqw * 32, 256, (int64_t)num_sms() * 32), 256, 0, s>>>(segs, cntq, ix->nqw, stage,
+                                                                                     qwoff, oi, oj, os);
         APS_LAUNCH_CHECK();
     }
     APS_CUDA(cudaStreamSynchronize(s));
@@ -911,9 +916,8 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
             P.stage = stage.p;
             P.stage_cap = stage_cap;
             P.stage_count = ctr.p + 5;
+            P.stage_slab = 256;  // query batches are small: keep the slab tails short
             P.segs = segs.p;
-            P.seg_cap = nqw;
-            P.seg_count = ctr.p + 6;
             P.cntq = cntq.p;
             P.counters = ctr.p;
             P.work = ctr.p + 8;
@@ -931,9 +935,13 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
         APS_CUDA(cudaMemcpyAsync(ch, ctr.p, sizeof(ch), cudaMemcpyDeviceToHost, s));
         APS_CUDA(cudaStreamSynchronize(s));
         if ((int64_t)ch[5] <= stage_cap) break;
-        stage_cap = (int64_t)ch[5];
+        stage_cap = (int64_t)ch[5] + (int64_t)grid * G * 256;  // what was reserved, plus one slab per group
     }
-    const int64_t npairs = (int64_t)ch[5], nseg = (int64_t)ch[6];
+    if ((int64_t)ch[5] > stage_cap) {
+        set_error("pair staging overflow persisted");
+        return APS_EOVERFLOW;
+    }
+    const int64_t npairs = (int64_t)ch[3];
     DBuf<int64_t> qwoff;
     APS_TRY(qwoff.alloc((size_t)nqw + 1, s));
     APS_TRY(scan_exclusive(cntq.p, qwoff.p, nqw, s));
@@ -949,9 +957,9 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
     int32_t *oi = reinterpret_cast<int32_t *>(blk);
     int32_t *oj = reinterpret_cast<int32_t *>(blk + seg4);
     float *os = reinterpret_cast<float *>(blk + 2 * seg4);
-    if (nseg > 0) {
-        k_gather<<<(unsigned)std::min<int64_t>(nseg, (int64_t)sms * 32), 256, 0, s>>>(segs.p, nseg, stage.p, qwoff.p,
-                                                                                      oi, oj, os);
+    if (npairs > 0) {
+        k_gather<<<grid_for(nqw * 32, 256, (int64_t)sms * 32), 256, 0, s>>>(segs.p, cntq.p, nqw, stage.p, qwoff.p, oi,
+                                                                           oj, os);
         APS_LAUNCH_CHECK();
     }
     APS_CUDA(cudaEventRecord(ev[2], s));
