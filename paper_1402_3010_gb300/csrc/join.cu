@@ -208,9 +208,11 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
         if (f_remscore ? qs >= xl : xl == 0) continue;
         // minsize: a match y needs |y| >= t / maxweight(x) (margin for rounding and the
         // 1e-3 norm tolerance); the size class byte of each entry is compared with it
+        // (float, directed rounding: numerator down, denominator up, quotient down, so the
+        // bound can only come out below its exact value and never prunes a match)
         int smin = 0;
         if (f_minsize && I.packed && mwx > 0.f)
-            smin = min(255, (int)ceil(((double)t - (double)beta) / ((double)mwx * 1.002)));
+            smin = (int)ceilf(fminf(__fdiv_rd(__fsub_rd(t, beta), __fmul_ru(mwx, 1.0020001f)), 255.f));
         const uint32_t smin_tag = (uint32_t)max(smin, 0) << 24;
         const int32_t idmask = I.packed ? 0x00ffffff : 0x7fffffff;
         const int ncreate = xl - qs;  // components walked first; they may create candidates
@@ -252,6 +254,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     }
                     cnt = (int32_t)(le - ls);
                     st = ls;
+                    n_visits += (unsigned long long)cnt;  // every entry of the window's list is walked
                 }
                 // scan of (chunks, non-empty, non-empty creating) packed in one int64
                 const int64_t nch = (cnt + 127) >> 7;
@@ -312,7 +315,6 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
 #pragma unroll
                         for (int u = 0; u < 4; u++)
                             ent[u] = (e0 + u * 32 < cen) ? __ldg(&P.post[e0 + u * 32]) : make_int2(0, 0);
-                        if (lane == 0) n_visits += (unsigned long long)min((int64_t)128, cen - e0);
 #pragma unroll
                         for (int u = 0; u < 4; u++) {
                             if (e0 + u * 32 >= cen) continue;
