@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=600, help="queries in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sparse", choices=["sparse", "dense", "batched", "serving"],
+    ap.add_argument("--workload", default="sparse", choices=["sparse", "dense", "batched", "serving", "ablation"],
                     help="sparse: the 200k-vector sparse self-join (default line); dense: the 200k x 256 "
                          "embedding self-join on the tensor cores; batched: 512 independent sparse "
                          "instances; serving: query batches against a 1M-vector resident index")
@@ -654,6 +654,94 @@ def run_reference(args, rank):
     }
 
 
+def run_ablation(args, rank, world):
+    """The paper's optimisation-variant matrix (Sec. 4, Tables 2-3) on the sparse workload:
+    each variant's index build + join, timed, with its work counters, and its pairs checked
+    against all-pairs-2's (identical keys, scores within 1e-5). Rank 0 only."""
+    import torch
+
+    import paper_1402_3010_gb300 as aps
+
+    if rank != 0:
+        return None
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    aps.load()
+    t = float(np.float32(args.t))
+    c = workload(args.n, args.m)
+    stream = torch.cuda.current_stream(dev)
+    ip = torch.from_numpy(c.indptr).to(dev)
+    ix = torch.from_numpy(c.idx).to(dev)
+    vv = torch.from_numpy(c.val).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    evals = c.n * (c.n - 1) // 2
+    order = ["all-pairs-2", "all-pairs-0-array", "all-pairs-0-remscore", "all-pairs-0-minsize", "all-pairs-1-array",
+             "all-pairs-1-remscore", "all-pairs-1-upperbound", "all-pairs-1-minsize", "all-pairs-1-remscore-minsize"]
+    ref = None
+    rows = []
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
+    for name in order:
+        flags = aps.VARIANTS[name]
+
+        def step(keep=False):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            flush.fill_(1.0)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            h = aps.aps_build_index(ip, ix, vv, c.n, c.m, t, flags, stream)
+            p = aps.aps_all_pairs(h)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            st = aps.aps_index_stats(h)
+            out = aps.pairs_to_numpy(p) if keep else None
+            aps.aps_pairs_free(p)
+            aps.aps_index_free(h)
+            return e0.elapsed_time(e1), st, out
+
+        step()  # warm-up (sizes the staging buffer)
+        times = []
+        for k in range(max(args.steps, 1)):
+            ms, st, out = step(keep=(k == 0))
+            times.append(ms)
+        i, j, s = out
+        keys = i.astype(np.int64) * c.n + j
+        if ref is None:
+            ref = (keys, s)
+            same, ds = True, 0.0
+        else:
+            same = bool(np.array_equal(keys, ref[0]))
+            ds = float(np.abs(s - ref[1]).max(initial=0.0)) if same else None
+        ms = statistics.median(times)
+        rows.append({"variant": name, "flags": flags, "ms_step": ms, "ms_build": st["ms_build"],
+                     "ms_join": st["ms_join"], "evaluations_per_s": evals / (ms * 1e-3),
+                     "visits": st["visits"], "candidates": st["candidates"], "verified": st["verified"],
+                     "pairs": st["pairs"], "band": st["band"], "same_pairs_as_all_pairs_2": same,
+                     "max_score_diff": ds})
+    clk = clocks.stop()
+    base = rows[0]
+    return {
+        "metric": METRIC,
+        "value": base["evaluations_per_s"],
+        "unit": UNIT,
+        "n_gpus": 1,
+        "steps": max(args.steps, 1),
+        "warmup": 1,
+        "ms_per_step": base["ms_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": "optimisation-variant matrix (paper Sec. 4, Tables 2-3) on " + WORKLOAD,
+                   "n": c.n, "m": c.m, "nnz": c.nnz, "t": t, "parallelism": "single GPU",
+                   "l2": "256 MB buffer written before each step (L2 flush)"},
+        "variants": rows,
+        "clocks": clk,
+    }
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -666,6 +754,8 @@ def main():
         line = run_batched(args)
     elif args.workload == "serving":
         line = run_serving(args)
+    elif args.workload == "ablation":
+        line = run_ablation(args, rank, world)
     else:
         line = run_aps(args, rank, world)
     if line is not None:

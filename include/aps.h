@@ -57,6 +57,21 @@ typedef enum aps_status {
 #define APS_NO_UPPERBOUND 0x40u   /* ablation: no upperbound before dot(x, y') */
 #define APS_HOST_OUTPUT 0x100u    /* results are copied to pinned host memory */
 
+/* The paper's sequential variants (Sec. 4; timed in Tables 2-3 of Sec. 7.3) as flag sets
+ * for aps_build_index. The candidate map is always a dense array here, so each is the
+ * paper's "-array" form; all-pairs-2 (every bound on) is the default. NO_UPPERBOUND also
+ * turns off the ||y'||_2 pre-filter, the other bound that skips dot(x, y'). Every variant
+ * returns the same pairs; they differ in work. */
+#define APS_VARIANT_ALL_PAIRS_0 (APS_NO_PARTIAL_INDEX | APS_NO_MINSIZE | APS_NO_REMSCORE | APS_NO_UPPERBOUND)
+#define APS_VARIANT_ALL_PAIRS_0_REMSCORE (APS_NO_PARTIAL_INDEX | APS_NO_MINSIZE | APS_NO_UPPERBOUND)
+#define APS_VARIANT_ALL_PAIRS_0_MINSIZE (APS_NO_PARTIAL_INDEX | APS_NO_REMSCORE | APS_NO_UPPERBOUND)
+#define APS_VARIANT_ALL_PAIRS_1 (APS_NO_MINSIZE | APS_NO_REMSCORE | APS_NO_UPPERBOUND)
+#define APS_VARIANT_ALL_PAIRS_1_REMSCORE (APS_NO_MINSIZE | APS_NO_UPPERBOUND)
+#define APS_VARIANT_ALL_PAIRS_1_UPPERBOUND (APS_NO_MINSIZE | APS_NO_REMSCORE)
+#define APS_VARIANT_ALL_PAIRS_1_MINSIZE (APS_NO_REMSCORE | APS_NO_UPPERBOUND)
+#define APS_VARIANT_ALL_PAIRS_1_REMSCORE_MINSIZE (APS_NO_UPPERBOUND)
+#define APS_VARIANT_ALL_PAIRS_2 0u
+
 /* ---- results -------------------------------------------------------------------- */
 typedef struct aps_pairs {
     int64_t count;   /* number of pairs */

@@ -40,6 +40,20 @@ NO_REMSCORE = 0x20
 NO_UPPERBOUND = 0x40
 HOST_OUTPUT = 0x100
 
+# The paper's sequential variants (Sec. 4, Tables 2-3) as aps_build_index flag sets; the
+# same values as the APS_VARIANT_* macros of aps.h.
+VARIANTS = {
+    "all-pairs-0-array": NO_PARTIAL_INDEX | NO_MINSIZE | NO_REMSCORE | NO_UPPERBOUND,
+    "all-pairs-0-remscore": NO_PARTIAL_INDEX | NO_MINSIZE | NO_UPPERBOUND,
+    "all-pairs-0-minsize": NO_PARTIAL_INDEX | NO_REMSCORE | NO_UPPERBOUND,
+    "all-pairs-1-array": NO_MINSIZE | NO_REMSCORE | NO_UPPERBOUND,
+    "all-pairs-1-remscore": NO_MINSIZE | NO_UPPERBOUND,
+    "all-pairs-1-upperbound": NO_MINSIZE | NO_REMSCORE,
+    "all-pairs-1-minsize": NO_REMSCORE | NO_UPPERBOUND,
+    "all-pairs-1-remscore-minsize": NO_UPPERBOUND,
+    "all-pairs-2": 0,
+}
+
 _P = ctypes.c_void_p
 _i32, _i64, _u32, _u64, _f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_float
 

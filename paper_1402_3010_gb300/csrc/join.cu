@@ -378,7 +378,8 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                         const int64_t gy = I.vbase + w0 + s;
                         sc = v;
                         // dot(x, y') <= ||y'||_2: most candidates stop here, on a 4-byte load
-                        if (v + __ldg(&P.pnorm[gy]) > t - beta) {
+                        // (a bound on the prefix dot like upperbound; both off with NO_UPPERBOUND)
+                        if (!f_upper || v + __ldg(&P.pnorm[gy]) > t - beta) {
                             ym = __ldg(&P.vmeta[gy]);
                             const int ys = ym.z;
                             bool ok = true;

@@ -86,3 +86,22 @@ def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
     monkeypatch.setattr(aps, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         aps.load()
+
+
+def test_variant_table_matches_header():
+    """The binding's VARIANTS table and the APS_VARIANT_* macros name the same flag sets."""
+    import paper_1402_3010_gb300 as A
+
+    txt = open(HEADER).read()
+    flags = {k: int(v, 16) for k, v in re.findall(r"#define (APS_NO_[A-Z_]+) (0x[0-9a-f]+)u", txt)}
+    macros = dict(re.findall(r"#define APS_VARIANT_([A-Z0-9_]+) (.+)", txt))
+    got = {}
+    for name, expr in macros.items():
+        v = 0
+        for tok in re.findall(r"APS_NO_[A-Z_]+", expr):
+            v |= flags[tok]
+        got["all-pairs-" + name[len("ALL_PAIRS_"):].lower().replace("_", "-")] = v
+    want = {("all-pairs-0" if k == "all-pairs-0-array" else "all-pairs-1" if k == "all-pairs-1-array" else k): v
+            for k, v in A.VARIANTS.items()}
+    assert got == want
+    assert len(got) == 9

@@ -112,6 +112,54 @@ def test_pruning_toggles_change_work_not_results(aps, build_flags, join_flags):
     compare(i, j, s, oracle.bruteforce(c, f32(t)), f32(t), c.n, csr=c, tol=2e-5 if build_flags & 2 else 1e-5)
 
 
+PAPER_VARIANTS = ["all-pairs-0-array", "all-pairs-0-remscore", "all-pairs-0-minsize", "all-pairs-1-array",
+                  "all-pairs-1-remscore", "all-pairs-1-upperbound", "all-pairs-1-minsize",
+                  "all-pairs-1-remscore-minsize", "all-pairs-2"]
+
+
+@pytest.mark.parametrize("name", PAPER_VARIANTS)
+def test_paper_variant_matches_oracle(aps, name):
+    """Each of the paper's sequential variants (Sec. 4, Tables 2-3) returns the exact set."""
+    import paper_1402_3010_gb300 as A
+
+    c = pl_small(43, n=3000, m=1800)
+    t = 0.6
+    i, j, s, _ = run_join(aps, c, t, A.VARIANTS[name])
+    compare(i, j, s, oracle.bruteforce(c, f32(t)), f32(t), c.n, csr=c)
+
+
+def test_paper_variants_only_remove_work(aps):
+    """Every bound only removes work: partial indexing never adds posting visits, remscore
+    never adds candidates, upperbound never adds prefix dots, minsize never adds candidates,
+    a full index has no prefix dots, and every variant returns the same pairs."""
+    import paper_1402_3010_gb300 as A
+
+    c = pl_small(44, n=6000, m=3000)
+    t = 0.7
+    W, out = {}, {}
+    for name in PAPER_VARIANTS:
+        i, j, s, st = run_join(aps, c, t, A.VARIANTS[name])
+        W[name] = st
+        out[name] = (i.astype(np.int64) * c.n + j, s)
+    assert W["all-pairs-1-array"]["visits"] <= W["all-pairs-0-array"]["visits"]
+    assert W["all-pairs-0-remscore"]["candidates"] <= W["all-pairs-0-array"]["candidates"]
+    assert W["all-pairs-1-remscore"]["candidates"] <= W["all-pairs-1-array"]["candidates"]
+    assert W["all-pairs-0-minsize"]["candidates"] <= W["all-pairs-0-array"]["candidates"]
+    assert W["all-pairs-1-minsize"]["candidates"] <= W["all-pairs-1-array"]["candidates"]
+    assert W["all-pairs-1-upperbound"]["verified"] <= W["all-pairs-1-array"]["verified"]
+    assert W["all-pairs-2"]["verified"] <= W["all-pairs-1-remscore-minsize"]["verified"]
+    for name in PAPER_VARIANTS[:3]:
+        assert W[name]["verified"] == 0
+    # the bounds prune for real on this input
+    assert W["all-pairs-2"]["candidates"] < W["all-pairs-1-array"]["candidates"]
+    assert W["all-pairs-1-array"]["visits"] < W["all-pairs-0-array"]["visits"]
+    k2, s2 = out["all-pairs-2"]
+    assert len(k2) > 0
+    for name in PAPER_VARIANTS:
+        assert np.array_equal(out[name][0], k2), name
+        assert np.abs(out[name][1] - s2).max(initial=0.0) <= 1e-5, name
+
+
 def test_host_and_device_inputs_agree(aps):
     c, t = synth.config_small(seed=5, n=800, m=2000)
     a = run_join(aps, c, t, device_input=True)
