@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=600, help="queries in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sparse", choices=["sparse", "dense", "batched", "serving", "ablation"],
+    ap.add_argument("--workload", default="sparse", choices=["sparse", "dense", "batched", "serving", "ablation", "graph"],
                     help="sparse: the 200k-vector sparse self-join (default line); dense: the 200k x 256 "
                          "embedding self-join on the tensor cores; batched: 512 independent sparse "
                          "instances; serving: query batches against a 1M-vector resident index")
@@ -742,6 +742,87 @@ def run_ablation(args, rank, world):
     }
 
 
+def run_graph(args, rank, world):
+    """The similarity graph G_S (Sec. 2.1) of the sparse workload's join result: CSR build
+    from the device pair list and k-nn (k = 16, Sec. 2.2), timed with CUDA events over
+    --steps repetitions (the join itself is untimed here). Rank 0 only."""
+    import torch
+
+    import paper_1402_3010_gb300 as aps
+
+    if rank != 0:
+        return None
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    aps.load()
+    t = float(np.float32(args.t))
+    c = workload(args.n, args.m)
+    stream = torch.cuda.current_stream(dev)
+    ip, ix, vv = (torch.from_numpy(a).to(dev) for a in (c.indptr, c.idx, c.val))
+    h = aps.aps_build_index(ip, ix, vv, c.n, c.m, t, 0, stream)
+    p = aps.aps_all_pairs(h)
+    aps.aps_index_free(h)
+    npairs = int(p.count)
+    k = 16
+    nbr = torch.empty((c.n, k), dtype=torch.int32, device=dev)
+    wk = torch.empty((c.n, k), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        flush.fill_(1.0)
+        e0.record(stream)
+        g = aps.aps_graph_csr(p, n=c.n, stream=stream)
+        e1.record(stream)
+        aps.aps_graph_knn(g, k, nbr, wk, stream=stream)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        nnz = int(g.nnz)
+        aps.aps_graph_free(g)
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), nnz
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
+    l0 = aps.aps_launch_count()
+    res = [step() for _ in range(args.steps)]
+    launches = aps.aps_launch_count() - l0
+    clk = clocks.stop()
+    aps.aps_pairs_free(p)
+    csr_ms = statistics.median(r[0] for r in res)
+    knn_ms = statistics.median(r[1] for r in res)
+    peak, peak_kind = peaks()
+    # algorithmic bytes of the CSR build: read the pair list once (12 B/pair), write both
+    # adjacency entries (2 x 8 B/pair) and row_ptr (8 B/vertex)
+    alg = 28 * npairs + 8 * (c.n + 1)
+    achieved = alg / (csr_ms * 1e-3) / 1e9
+    return {
+        "metric": "similarity-graph edges/s",
+        "value": npairs / (csr_ms * 1e-3),
+        "unit": "undirected edges/s (CSR build)",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": max(args.warmup, 3),
+        "ms_per_step": csr_ms + knn_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32/f32",
+        "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": "similarity graph G_S (CSR adjacency + k-nn, k=16) of " + WORKLOAD,
+                   "n": c.n, "m": c.m, "t": t, "edges": npairs, "adjacency_entries": 2 * npairs,
+                   "parallelism": "single GPU", "l2": "256 MB buffer written before each step (L2 flush)"},
+        "phases_ms": {"csr": csr_ms, "knn16": knn_ms},
+        "roofline": {"bound": "hbm", "kernel": "graph CSR build (counts, scans, j-sort, fills)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind + " (hbm_gbs, copy bandwidth)", "traffic": None,
+                     "alg_bytes_per_launch": alg, "ms_per_launch": csr_ms},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -756,6 +837,8 @@ def main():
         line = run_serving(args)
     elif args.workload == "ablation":
         line = run_ablation(args, rank, world)
+    elif args.workload == "graph":
+        line = run_graph(args, rank, world)
     else:
         line = run_aps(args, rank, world)
     if line is not None:

@@ -83,6 +83,18 @@ typedef struct aps_pairs {
     void *_priv;     /* library bookkeeping; do not touch */
 } aps_pairs;
 
+/* The similarity graph G_S(V, t) = (V, M) of Sec. 2.1 (edge u <-> v for every match,
+ * weight w(u, v) = u.v) as a CSR adjacency. */
+typedef struct aps_graph {
+    int32_t n;         /* vertices */
+    int32_t on_device; /* 1: the arrays are device pointers; 0: pinned host memory */
+    int64_t nnz;       /* adjacency entries = 2 x pairs */
+    int64_t *row_ptr;  /* [n + 1] row v is col[row_ptr[v] .. row_ptr[v + 1]) */
+    int32_t *col;      /* [nnz] neighbours of each vertex, in increasing id */
+    float *w;          /* [nnz] edge weights (the pairs' scores) */
+    void *_priv;       /* library bookkeeping; do not touch */
+} aps_graph;
+
 /* Work counters and phase times of the last aps_all_pairs / aps_query / batch call on
  * an index (all counts are exact; times are CUDA-event milliseconds). */
 typedef struct aps_stats {
@@ -216,6 +228,29 @@ aps_status aps_batch_all_pairs_csr(int32_t k, const int64_t *row_offsets, const 
  * multiple of 64 and at most 512. Needs an sm_103a device. */
 aps_status aps_all_pairs_dense(const float *X, int32_t n, int32_t d, float t, uint32_t flags,
                                void *stream, aps_pairs *out, aps_stats *stats);
+
+/* ---- the similarity graph -------------------------------------------------------- */
+/* CSR adjacency of G_S (Sec. 2.1) from a pair list: each pair (i[p], j[p], s[p]) gives the
+ * entries i -> j and j -> i of weight s[p]. The pairs must satisfy 0 <= i < j < n and be
+ * strictly increasing in (i, j), the order aps_all_pairs returns (so a result's arrays
+ * can be passed straight in with APS_DEVICE_PTRS when it is on the device); they are
+ * host pointers without that flag. APS_HOST_OUTPUT copies the graph to pinned host
+ * memory. Each row lists its neighbours in increasing id. count < 2^32.
+ * Errors: APS_EINVAL for a pair out of range, out of order or repeated (nothing is
+ * allocated then); APS_ENOMEM. Free with aps_graph_free. stream: cudaStream_t or NULL. */
+aps_status aps_graph_csr(const int32_t *i, const int32_t *j, const float *s, int64_t count, int32_t n,
+                         uint32_t flags, void *stream, aps_graph *out);
+/* The k nearest neighbours of every vertex read off a device graph (the k-nn use of the
+ * similarity graph, Sec. 2.2): row v of nbr[n * k] / wk[n * k] holds v's neighbours of
+ * largest weight, ties by smaller id, in that order; rows with fewer than k neighbours
+ * end in id -1, weight 0. nbr and wk are caller buffers, device pointers with
+ * APS_DEVICE_PTRS and host pointers otherwise. 1 <= k <= 256. */
+aps_status aps_graph_knn(const aps_graph *g, int32_t k, int32_t *nbr, float *wk, uint32_t flags,
+                         void *stream);
+/* Copy a graph's arrays (device or host) into caller buffers of n + 1 / nnz / nnz
+ * elements (any of them may be NULL). Synchronous. */
+aps_status aps_graph_copy_to(const aps_graph *g, int64_t *row_ptr, int32_t *col, float *w, void *stream);
+void aps_graph_free(aps_graph *g);
 
 /* ---- serving -------------------------------------------------------------------- */
 typedef struct aps_server aps_server;

@@ -18,6 +18,8 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                        dataset-statistics definitions of Table 1 (tests/golden/)
   bruteforce_cross     pinned to scipy.sparse FP64 Q.D^T + threshold
   dense_all_pairs      a library routine (NumPy matmul) -- it is itself the pin
+  graph_csr            pinned to a hand-worked graph and to scipy.sparse (A + A^T).tocsr()
+  graph_knn            pinned to a hand-worked graph, tie and padding cases, and heapq
 """
 from __future__ import annotations
 
@@ -262,3 +264,35 @@ def dense_rows(X: np.ndarray, t: float, rows) -> Pairs:
     a, b = rows[r[keep]], cidx[keep]
     s = blk[r[keep], cidx[keep]]
     return Pairs(np.minimum(a, b), np.maximum(a, b), s)
+
+
+def graph_csr(i, j, s, n: int):
+    """The similarity graph G_S(V, t) = (V, M) of Sec. 2.1: an undirected edge u <-> v of
+    weight w(u, v) = u.v for every match. Rows of its adjacency, neighbours in increasing
+    id: (row_ptr[n + 1], col, w)."""
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    s = np.asarray(s, dtype=np.float32)
+    src = np.concatenate([i, j])
+    dst = np.concatenate([j, i])
+    wt = np.concatenate([s, s])
+    order = np.lexsort((dst, src))  # by vertex, then by neighbour id
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(src, minlength=n), out=row_ptr[1:])
+    return row_ptr, dst[order].astype(np.int32), wt[order]
+
+
+def graph_knn(row_ptr, col, w, k: int):
+    """k-nn read off the similarity graph (Sec. 2.2): for each vertex its k neighbours of
+    largest weight, ties by smaller id, padded with (-1, 0). Returns (nbr[n, k], w[n, k])."""
+    n = len(row_ptr) - 1
+    nbr = np.full((n, k), -1, dtype=np.int32)
+    wk = np.zeros((n, k), dtype=np.float32)
+    for v in range(n):
+        a, b = int(row_ptr[v]), int(row_ptr[v + 1])
+        c, x = col[a:b], np.asarray(w[a:b], dtype=np.float64)
+        o = np.lexsort((c, -x))[:k]
+        nbr[v, : len(o)] = c[o]
+        wk[v, : len(o)] = x[o]
+    return nbr, wk
+

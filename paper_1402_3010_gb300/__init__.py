@@ -63,6 +63,11 @@ class aps_pairs(ctypes.Structure):
                 ("_reserved", _i32), ("_priv", _P)]
 
 
+class aps_graph(ctypes.Structure):
+    _fields_ = [("n", _i32), ("on_device", _i32), ("nnz", _i64), ("row_ptr", _P), ("col", _P), ("w", _P),
+                ("_priv", _P)]
+
+
 class aps_stats(ctypes.Structure):
     _fields_ = [("visits", _i64), ("candidates", _i64), ("verified", _i64), ("pairs", _i64),
                 ("band", _i64), ("evaluations", _i64), ("reruns", _i64), ("ms_build", _f32),
@@ -133,6 +138,10 @@ def load():
             "aps_debug_fail_alloc": (None, [_i64]),
             "aps_launch_count": (_i64, []),
             "aps_all_pairs_noalloc": (_i32, [_P, _P, _P, _P, _i64, ctypes.POINTER(_i64), _P]),
+            "aps_graph_csr": (_i32, [_P, _P, _P, _i64, _i32, _u32, _P, ctypes.POINTER(aps_graph)]),
+            "aps_graph_knn": (_i32, [ctypes.POINTER(aps_graph), _i32, _P, _P, _u32, _P]),
+            "aps_graph_copy_to": (_i32, [ctypes.POINTER(aps_graph), _P, _P, _P, _P]),
+            "aps_graph_free": (None, [ctypes.POINTER(aps_graph)]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -406,3 +415,59 @@ def aps_stream_cancel(server: int, ticket: int) -> None:
 def aps_server_free(server: int) -> None:
     if server:
         load().aps_server_free(server)
+
+
+def aps_graph_csr(i, j=None, s=None, n: int = 0, flags: int = 0, stream=None) -> aps_graph:
+    """CSR adjacency of the similarity graph from a pair list: an aps_pairs result, or
+    i, j, s as host NumPy or device torch arrays (int32, int32, float32)."""
+    lib = load()
+    g = aps_graph()
+    if isinstance(i, aps_pairs):
+        p = i
+        ptrs, count = (p.i, p.j, p.score), int(p.count)
+        flags |= DEVICE_PTRS if p.on_device else 0
+        keep = (p,)
+    elif _is_torch(i):
+        for a, dt in ((i, "int32"), (j, "int32"), (s, "float32")):
+            if not a.is_cuda or str(a.dtype) != f"torch.{dt}" or not a.is_contiguous():
+                raise TypeError(f"device pair arrays must be contiguous CUDA {dt} tensors")
+        ptrs, count, keep = (_ptr(i), _ptr(j), _ptr(s)), int(i.numel()), (i, j, s)
+        flags |= DEVICE_PTRS
+    else:
+        a = np.ascontiguousarray(i, dtype=np.int32)
+        b = np.ascontiguousarray(j, dtype=np.int32)
+        c = np.ascontiguousarray(s, dtype=np.float32)
+        ptrs, count, keep = (a.ctypes.data, b.ctypes.data, c.ctypes.data), int(a.size), (a, b, c)
+    _check(lib.aps_graph_csr(*ptrs, count, int(n), flags, _stream_ptr(stream), ctypes.byref(g)), "aps_graph_csr")
+    del keep
+    return g
+
+
+def aps_graph_knn(g: aps_graph, k: int, nbr=None, wk=None, stream=None):
+    """k nearest neighbours per vertex: (nbr[n, k], wk[n, k]); NumPy host arrays unless
+    torch CUDA tensors are passed in."""
+    lib = load()
+    flags = 0
+    if nbr is None:
+        nbr = np.empty((g.n, k), np.int32)
+        wk = np.empty((g.n, k), np.float32)
+    elif _is_torch(nbr):
+        flags |= DEVICE_PTRS
+    _check(lib.aps_graph_knn(ctypes.byref(g), int(k), _ptr(nbr), _ptr(wk), flags, _stream_ptr(stream)),
+           "aps_graph_knn")
+    return nbr, wk
+
+
+def graph_to_numpy(g: aps_graph):
+    """(row_ptr, col, w) NumPy copies of a graph."""
+    rp = np.empty(g.n + 1, np.int64)
+    col = np.empty(g.nnz, np.int32)
+    w = np.empty(g.nnz, np.float32)
+    _check(load().aps_graph_copy_to(ctypes.byref(g), rp.ctypes.data, col.ctypes.data, w.ctypes.data, None),
+           "aps_graph_copy_to")
+    return rp, col, w
+
+
+def aps_graph_free(g: aps_graph) -> None:
+    load().aps_graph_free(ctypes.byref(g))
+

@@ -482,4 +482,34 @@ const char *aps_version(void) { return "aps 0.1 (sm_103a)"; }
 
 void aps_debug_fail_alloc(int64_t k) { set_alloc_fault(k); }
 
+aps_status aps_graph_csr(const int32_t *i, const int32_t *j, const float *s, int64_t count, int32_t n,
+                         uint32_t flags, void *stream, aps_graph *out) {
+    if (!out) {
+        set_error("out must not be NULL");
+        return APS_EINVAL;
+    }
+    return graph_csr(i, j, s, count, n, flags, static_cast<cudaStream_t>(stream), out);
+}
+
+aps_status aps_graph_knn(const aps_graph *g, int32_t k, int32_t *nbr, float *wk, uint32_t flags, void *stream) {
+    return graph_knn(g, k, nbr, wk, flags, static_cast<cudaStream_t>(stream));
+}
+
+aps_status aps_graph_copy_to(const aps_graph *g, int64_t *row_ptr, int32_t *col, float *w, void *stream) {
+    if (!g || !g->_priv) {
+        set_error("the graph must come from aps_graph_csr");
+        return APS_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (row_ptr) APS_CUDA(cudaMemcpyAsync(row_ptr, g->row_ptr, 8 * ((size_t)g->n + 1), cudaMemcpyDefault, s));
+    if (g->nnz) {
+        if (col) APS_CUDA(cudaMemcpyAsync(col, g->col, 4 * (size_t)g->nnz, cudaMemcpyDefault, s));
+        if (w) APS_CUDA(cudaMemcpyAsync(w, g->w, 4 * (size_t)g->nnz, cudaMemcpyDefault, s));
+    }
+    APS_CUDA(cudaStreamSynchronize(s));
+    return APS_OK;
+}
+
+void aps_graph_free(aps_graph *g) { graph_release(g); }
+
 }  // extern "C"

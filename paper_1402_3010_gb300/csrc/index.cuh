@@ -88,6 +88,13 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
                                   aps_stats *stats);
 double dense_margin(int d);
 
+// The similarity graph G_S as a CSR adjacency from a pair list, its k nearest neighbours,
+// and its release (graph.cu).
+aps_status graph_csr(const int32_t *i, const int32_t *j, const float *s, int64_t count, int32_t n, uint32_t flags,
+                     cudaStream_t st, aps_graph *out);
+aps_status graph_knn(const aps_graph *g, int32_t k, int32_t *nbr, float *wk, uint32_t flags, cudaStream_t s);
+void graph_release(aps_graph *g);
+
 }  // namespace aps
 
 struct aps_index {
@@ -170,5 +177,12 @@ aps_status dense_all_pairs(const float *X, int32_t n, int32_t d, float t, uint32
 aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t, cudaStream_t s, aps_pairs *out,
                                   aps_stats *stats);
 double dense_margin(int d);
+
+// The similarity graph G_S as a CSR adjacency from a pair list, its k nearest neighbours,
+// and its release (graph.cu).
+aps_status graph_csr(const int32_t *i, const int32_t *j, const float *s, int64_t count, int32_t n, uint32_t flags,
+                     cudaStream_t st, aps_graph *out);
+aps_status graph_knn(const aps_graph *g, int32_t k, int32_t *nbr, float *wk, uint32_t flags, cudaStream_t s);
+void graph_release(aps_graph *g);
 
 }  // namespace aps

@@ -346,3 +346,28 @@ def serving_arrivals(num_batches: int, rate_per_s: float, seed: int = 56):
     gaps = rng.exponential(1.0 / rate_per_s, size=num_batches)
     sizes = np.exp(rng.uniform(0.0, math.log(4096.0), size=num_batches)).astype(np.int64)
     return np.cumsum(gaps), np.clip(sizes, 1, 4096)
+
+
+def pair_list(n: int, count: int, seed: int, skew: float = 0.0, w_lo: float = 0.5):
+    """A seeded pair list in the form the join returns: unique (i < j) pairs strictly
+    increasing in (i, j), float32 weights U[w_lo, 1). Endpoints are drawn with probability
+    ~ (rank + 1)^-skew over a random vertex permutation (skew 0: uniform; larger: hubs).
+    Up to `count` pairs (duplicates and self-pairs are dropped)."""
+    rng = np.random.default_rng(seed)
+    if n < 2 or count <= 0:
+        e = np.zeros(0, dtype=np.int32)
+        return e, e.copy(), np.zeros(0, dtype=np.float32)
+    p = (np.arange(n, dtype=np.float64) + 1.0) ** (-skew)
+    p /= p.sum()
+    perm = rng.permutation(n)
+    a = perm[rng.choice(n, size=count, p=p)]
+    b = perm[rng.choice(n, size=count, p=p)]
+    keep = a != b
+    lo = np.minimum(a[keep], b[keep]).astype(np.int64)
+    hi = np.maximum(a[keep], b[keep]).astype(np.int64)
+    key = np.unique(lo * n + hi)
+    i = (key // n).astype(np.int32)
+    j = (key % n).astype(np.int32)
+    s = rng.uniform(w_lo, 1.0, size=key.size).astype(np.float32)
+    return i, j, s
+
