@@ -191,26 +191,54 @@ __global__ void rs_hist_kernel(const uint64_t *__restrict__ keys, int64_t n, int
     hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// Stable scatter: items are visited in input order (round by round, lane order inside a
-// warp, warp order inside a round), and each lands after all earlier items of its digit.
-__global__ void rs_scatter_kernel(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                                  uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
-                                  int shift, const int64_t *__restrict__ offs) {
-    __shared__ int64_t base[RS_DIGITS];
-    __shared__ int64_t wc[RS_WARPS][RS_DIGITS];
+// Stable scatter: a tile is first ranked into shared memory by digit (items visited in
+// input order: round by round, lane order inside a warp, warp order inside a round), then
+// written out in digit runs, each run to consecutive addresses after all earlier items of
+// its digit. rs_smem holds the tile's keys and values (RS_TILE each).
+constexpr int RS_SMEM = RS_TILE * (8 + 4);
+
+__global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const uint64_t *__restrict__ kin,
+                                                                  const uint32_t *__restrict__ vin,
+                                                                  uint64_t *__restrict__ kout,
+                                                                  uint32_t *__restrict__ vout, int64_t n, int shift,
+                                                                  const int64_t *__restrict__ offs) {
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(rs_smem);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sk + RS_TILE);
+    __shared__ int64_t gbase[RS_DIGITS];  // output offset of (digit, this tile)
+    __shared__ int32_t lbase[RS_DIGITS];  // tile-local start of each digit
+    __shared__ int32_t cur[RS_DIGITS];    // tile-local cursor of each digit
+    __shared__ int32_t wc[RS_WARPS][RS_DIGITS];
+    __shared__ int32_t wsum[RS_WARPS];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    base[t] = offs[(int64_t)t * gridDim.x + blockIdx.x];
+    const int64_t nb = gridDim.x;
+    const int64_t hi = (int64_t)t * nb + blockIdx.x;
+    gbase[t] = offs[hi];
+    // exclusive scan of the tile's digit counts (offs is the digit-major scan of them)
+    const int c = (int)(offs[hi + 1] - offs[hi]);
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; w++) before += wsum[w];
+    lbase[t] = before + inc - c;
+    cur[t] = before + inc - c;
     const unsigned lt_mask = (1u << lane) - 1u;
-    int64_t tile = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t tile = (int64_t)blockIdx.x * RS_TILE;
     for (int r = 0; r < RS_ROUNDS; r++) {
         for (int w = 0; w < RS_WARPS; w++) wc[w][t] = 0;
         __syncthreads();
-        int64_t i = tile + (int64_t)r * RS_THREADS + t;
-        bool valid = i < n;
-        uint64_t k = valid ? kin[i] : 0;
-        uint32_t v = valid ? vin[i] : 0;
-        int d = (int)((k >> shift) & 0xff);
-        unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        const int64_t i = tile + (int64_t)r * RS_THREADS + t;
+        const bool valid = i < n;
+        const uint64_t k = valid ? kin[i] : 0;
+        const uint32_t v = valid ? vin[i] : 0;
+        const int d = (int)((k >> shift) & 0xff);
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
         unsigned peers = 0;
         int rank = 0;
         if (valid) {
@@ -219,22 +247,31 @@ __global__ void rs_scatter_kernel(const uint64_t *__restrict__ kin, const uint32
             if (rank == 0) wc[warp][d] = __popc(peers);
         }
         __syncthreads();
-        {  // per digit: turn warp counts into absolute warp bases
-            int64_t acc = base[t];
+        {  // per digit: warp counts -> tile-local warp bases
+            int acc = cur[t];
             for (int w = 0; w < RS_WARPS; w++) {
-                int64_t c = wc[w][t];
+                const int cw = wc[w][t];
                 wc[w][t] = acc;
-                acc += c;
+                acc += cw;
             }
-            base[t] = acc;
+            cur[t] = acc;
         }
         __syncthreads();
         if (valid) {
-            int64_t dst = wc[warp][d] + rank;
-            kout[dst] = k;
-            vout[dst] = v;
+            const int q = wc[warp][d] + rank;
+            sk[q] = k;
+            sv[q] = v;
         }
         __syncthreads();
+    }
+    // write out in tile order: consecutive items of a digit go to consecutive addresses
+    const int tn = (int)min((int64_t)RS_TILE, n - tile);
+    for (int q = t; q < tn; q += RS_THREADS) {
+        const uint64_t k = sk[q];
+        const int d = (int)((k >> shift) & 0xff);
+        const int64_t dst = gbase[d] + (q - lbase[d]);
+        kout[dst] = k;
+        vout[dst] = sv[q];
     }
 }
 
@@ -252,6 +289,7 @@ aps_status sort_pairs(uint64_t *keys, uint32_t *vals, int64_t n, int bits, cudaS
     APS_TRY(v2.alloc((size_t)n, s));
     APS_TRY(hist.alloc((size_t)(nb * RS_DIGITS), s));
     APS_TRY(offs.alloc((size_t)(nb * RS_DIGITS + 1), s));
+    APS_CUDA(cudaFuncSetAttribute(rs_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM));
     uint64_t *ka = keys, *kb = k2.p;
     uint32_t *va = vals, *vb = v2.p;
     for (int p = 0; p < passes; p++) {
@@ -259,7 +297,7 @@ aps_status sort_pairs(uint64_t *keys, uint32_t *vals, int64_t n, int bits, cudaS
         rs_hist_kernel<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, n, shift, hist.p);
         APS_LAUNCH_CHECK();
         APS_TRY(scan_exclusive(hist.p, offs.p, nb * RS_DIGITS, s));
-        rs_scatter_kernel<<<(unsigned)nb, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, offs.p);
+        rs_scatter_kernel<<<(unsigned)nb, RS_THREADS, RS_SMEM, s>>>(ka, va, kb, vb, n, shift, offs.p);
         APS_LAUNCH_CHECK();
         uint64_t *tk = ka;
         ka = kb;
