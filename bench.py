@@ -157,6 +157,23 @@ def cpu_baseline(c, t, sample):
     }
 
 
+def measured_traffic(profile: str, source: str, t: float):
+    """DRAM bytes per launch from a committed ncu capture (profiles/<profile>), valid only
+    while the kernel source is byte-identical to the one the counters were taken from."""
+    import hashlib
+
+    prof = os.path.join(ROOT, "profiles", profile)
+    if not os.path.exists(prof):
+        return None
+    with open(prof) as f:
+        tr = json.load(f)
+    with open(os.path.join(ROOT, "paper_1402_3010_gb300", "csrc", source), "rb") as f:
+        cur = hashlib.sha1(f.read()).hexdigest()[:16]
+    if tr.get("source_sha1_16") == cur and abs(tr.get("t", -1) - t) < 1e-7:
+        return tr.get("dram_bytes_per_launch")
+    return None
+
+
 # ------------------------------------------------------------------ the GPU arm
 def run_aps(args, rank, world):
     import torch
@@ -267,18 +284,7 @@ def run_aps(args, rank, world):
     alg_bytes = 8 * last["visits"] + 8 * last["candidates"] + 16 * last["verified"] + 8 * last["pairs"]
     jm = statistics.mean(join_ms)
     achieved = alg_bytes / (jm * 1e-3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "join_kernel_traffic.json")
-    if os.path.exists(prof) and c.n == 200_000 and c.m == 100_000:
-        # valid only while the kernel source is the one the counters were taken from
-        import hashlib
-
-        with open(prof) as f:
-            tr = json.load(f)
-        with open(os.path.join(ROOT, "paper_1402_3010_gb300", "csrc", "join.cu"), "rb") as f:
-            cur = hashlib.sha1(f.read()).hexdigest()[:16]
-        if tr.get("source_sha1_16") == cur and abs(tr.get("t", -1) - t) < 1e-7:
-            traffic = tr.get("dram_bytes_per_launch")
+    traffic = measured_traffic("join_kernel_traffic.json", "join.cu", t) if (c.n, c.m) == (200_000, 100_000) else None
     line = {
         "metric": METRIC,
         "value": world * evals * args.steps / (ms * 1e-3),
@@ -426,7 +432,9 @@ def run_dense(args, rank, world):
                    "evaluations_per_step": evals},
         "roofline": {"bound": "tensor", "kernel": "dense_gemm_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_kind": kind + " (bf16_tflops burst, cuBLAS 8192^3)", "traffic": None,
+                     "peak_kind": kind + " (bf16_tflops burst, cuBLAS 8192^3)",
+                     "traffic": measured_traffic("dense_gemm_traffic.json", "dense.cu", t) if (n, d) == (200_000, 256)
+                     else None,
                      "alg_flops_per_launch": flops, "ms_per_launch": gm},
         "phases_ms": {"gemm": gm, "sort_rescore_compact": st["ms_sort"], "call": st["ms_total"]},
         "work": {k: st[k] for k in ("candidates", "pairs", "band")},
