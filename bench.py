@@ -45,13 +45,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--t", type=float, default=0.7)
+    ap.add_argument("--ranks", type=int, default=2, help="host ranks of --workload horizontal")
     ap.add_argument("--impl", default="aps", choices=["aps", "reference"])
     ap.add_argument("--n", type=int, default=200_000)
     ap.add_argument("--m", type=int, default=100_000)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=600, help="queries in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sparse", choices=["sparse", "dense", "batched", "serving", "ablation", "graph"],
+    ap.add_argument("--workload", default="sparse", choices=["sparse", "dense", "batched", "serving", "ablation", "graph", "horizontal"],
                     help="sparse: the 200k-vector sparse self-join (default line); dense: the 200k x 256 "
                          "embedding self-join on the tensor cores; batched: 512 independent sparse "
                          "instances; serving: query batches against a 1M-vector resident index")
@@ -831,6 +832,110 @@ def run_graph(args, rank, world):
     }
 
 
+def _horizontal_rank(rank, p, port, n, m, t, out_q):
+    """One host rank of --workload horizontal (a spawned process)."""
+    from datetime import timedelta
+
+    import torch
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    from paper_1402_3010_gb300 import horizontal as H
+
+    torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
+    c = workload(n, m)
+    store = dist.TCPStore("127.0.0.1", port, p, rank == 0, timedelta(seconds=900))
+    part_of = lambda r: H.cyclic_part(c.indptr, c.idx, c.val, c.m, r, p)  # noqa: E731
+    matcher = H.GpuMatcher()
+    store.set(f"ready/{rank}", b"1")
+    store.wait([f"ready/{r}" for r in range(p)])
+    t0 = time.perf_counter()
+    res = H.horizontal_all_pairs(rank, p, store, part_of, t, matcher, timeout_s=900.0)
+    dt = time.perf_counter() - t0
+    info = {"rank": rank, "seconds": dt, "part_bytes": int(part_of(rank).indptr.nbytes + part_of(rank).idx.nbytes
+                                                           + part_of(rank).val.nbytes)}
+    if res is not None:
+        i, j, s_, failed = res
+        info.update(pairs=int(i.size), keysum=int((i.astype(np.int64) * n + j).sum() % (1 << 61)), failed=failed)
+    out_q.put(info)
+
+
+def run_horizontal(args, rank, world):
+    """§8 row f4: the horizontal driver (Sec. 5.2, Alg. 6) with --ranks host processes
+    on this machine's GPU(s), against the single-process join of the same workload."""
+    import multiprocessing as mp
+    import socket
+
+    import torch
+
+    import paper_1402_3010_gb300 as aps
+
+    if rank != 0:
+        return None
+    aps.load()
+    t = float(np.float32(args.t))
+    c = workload(args.n, args.m)
+    dev = torch.device("cuda", 0)
+    ip, ix, vv = (torch.from_numpy(a).to(dev) for a in (c.indptr, c.idx, c.val))
+    h = aps.aps_build_index(ip, ix, vv, c.n, c.m, t)
+    pr = aps.aps_all_pairs(h)
+    i, j, _ = aps.pairs_to_numpy(pr)
+    aps.aps_pairs_free(pr)
+    aps.aps_index_free(h)
+    ref_pairs, ref_sum = int(i.size), int((i.astype(np.int64) * c.n + j).sum() % (1 << 61))
+    del ip, ix, vv
+    torch.cuda.empty_cache()
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = args.ranks
+    procs = [ctx.Process(target=_horizontal_rank, args=(r, p, port, args.n, args.m, t, q)) for r in range(p)]
+    for x in procs:
+        x.start()
+    infos = []
+    deadline = time.time() + 1200
+    while len(infos) < p and time.time() < deadline:
+        try:
+            infos.append(q.get(timeout=5))
+        except Exception:
+            if not any(x.is_alive() for x in procs):  # every rank exited: nothing more will come
+                break
+    for x in procs:
+        x.join(30)
+        if x.is_alive():
+            x.kill()
+    if len(infos) < p:
+        return {"metric": METRIC, "value": None, "unit": UNIT, "error": f"{p - len(infos)} of {p} ranks returned nothing"}
+    secs = max(x["seconds"] for x in infos)
+    root = [x for x in infos if x["rank"] == 0][0]
+    part_bytes = {x["rank"]: x["part_bytes"] for x in infos}
+    exchanged = sum(part_bytes[a] for b in range(p) for a in range(b))
+    evals = c.n * (c.n - 1) // 2
+    return {
+        "metric": METRIC,
+        "value": evals / secs,
+        "unit": UNIT,
+        "n_gpus": max(torch.cuda.device_count(), 1),
+        "steps": 1,
+        "warmup": 0,
+        "ms_per_step": 1000 * secs,
+        "higher_is_better": True,
+        "scaling": "strong",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": f"horizontal driver (Sec. 5.2, Alg. 6), {p} host ranks, on " + WORKLOAD,
+                   "n": c.n, "m": c.m, "t": t, "parallelism": f"{p} host processes, vector-partitioned (cyclic)",
+                   "exchange": "TCPStore key-value store on 127.0.0.1"},
+        "horizontal": {"ranks": p, "wall_s_per_rank": {x["rank"]: x["seconds"] for x in infos},
+                       "pairs": root["pairs"], "same_pairs_as_single_process": root["pairs"] == ref_pairs
+                       and root["keysum"] == ref_sum, "failed_ranks": root["failed"],
+                       "vector_bytes_exchanged": exchanged},
+    }
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -847,6 +952,8 @@ def main():
         line = run_ablation(args, rank, world)
     elif args.workload == "graph":
         line = run_graph(args, rank, world)
+    elif args.workload == "horizontal":
+        line = run_horizontal(args, rank, world)
     else:
         line = run_aps(args, rank, world)
     if line is not None:
