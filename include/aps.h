@@ -56,6 +56,9 @@ typedef enum aps_status {
 #define APS_NO_REMSCORE 0x20u     /* ablation: no remscore admission bound */
 #define APS_NO_UPPERBOUND 0x40u   /* ablation: no upperbound before dot(x, y') */
 #define APS_HOST_OUTPUT 0x100u    /* results are copied to pinned host memory */
+#define APS_SUBUNIT_NORMS 0x200u  /* rows may have L2 norm below 1 (at most 1 + 1e-3), e.g. the
+                                     projection of unit vectors onto a block of dimensions; every
+                                     pruning bound of the join holds for such rows */
 
 /* The paper's sequential variants (Sec. 4; timed in Tables 2-3 of Sec. 7.3) as flag sets
  * for aps_build_index. The candidate map is always a dense array here, so each is the
@@ -251,6 +254,20 @@ aps_status aps_graph_knn(const aps_graph *g, int32_t k, int32_t *nbr, float *wk,
  * elements (any of them may be NULL). Synchronous. */
 aps_status aps_graph_copy_to(const aps_graph *g, int64_t *row_ptr, int32_t *col, float *w, void *stream);
 void aps_graph_free(aps_graph *g);
+
+/* ---- exact verification of candidate pairs --------------------------------------- */
+/* The score merge of the vertical algorithm with local pruning (Sec. 5.1, Lemma 1 and
+ * Eq. 1: a match has a partial score >= t/p on at least one of p dimension blocks): the
+ * union of k candidate lists `lists[0..k)` (pairs i < j of the same n vectors, device or
+ * host results, any order, duplicates allowed) is deduplicated, each pair's dot product is
+ * recomputed in float64 from the rows of the CSR (indptr/idx/val as for aps_build_index,
+ * device pointers with APS_DEVICE_PTRS; each row's ids strictly increasing), and the pairs
+ * with dot >= t are returned in (i, j) order with float32 scores (free with aps_pairs_free).
+ * *n_candidates (may be NULL) receives the size of the union. APS_HOST_OUTPUT as for
+ * aps_all_pairs. Errors: APS_EINVAL for a pair outside 0 <= i < j < n or a malformed row. */
+aps_status aps_pairs_verify(const aps_pairs *lists, int32_t k, const int64_t *indptr, const int32_t *idx,
+                            const float *val, int32_t n, int32_t m, float t, uint32_t flags, void *stream,
+                            aps_pairs *out, int64_t *n_candidates);
 
 /* ---- serving -------------------------------------------------------------------- */
 typedef struct aps_server aps_server;

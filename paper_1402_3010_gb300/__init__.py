@@ -39,6 +39,7 @@ NO_MINSIZE = 0x10
 NO_REMSCORE = 0x20
 NO_UPPERBOUND = 0x40
 HOST_OUTPUT = 0x100
+SUBUNIT_NORMS = 0x200
 
 # The paper's sequential variants (Sec. 4, Tables 2-3) as aps_build_index flag sets; the
 # same values as the APS_VARIANT_* macros of aps.h.
@@ -142,6 +143,8 @@ def load():
             "aps_graph_knn": (_i32, [ctypes.POINTER(aps_graph), _i32, _P, _P, _u32, _P]),
             "aps_graph_copy_to": (_i32, [ctypes.POINTER(aps_graph), _P, _P, _P, _P]),
             "aps_graph_free": (None, [ctypes.POINTER(aps_graph)]),
+            "aps_pairs_verify": (_i32, [ctypes.POINTER(aps_pairs), _i32, _P, _P, _P, _i32, _i32, _f32, _u32, _P,
+                                        ctypes.POINTER(aps_pairs), ctypes.POINTER(_i64)]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -470,4 +473,20 @@ def graph_to_numpy(g: aps_graph):
 
 def aps_graph_free(g: aps_graph) -> None:
     load().aps_graph_free(ctypes.byref(g))
+
+
+def aps_pairs_verify(lists, indptr, idx, val, n: int, m: int, t: float, flags: int = 0, stream=None):
+    """Union of candidate pair lists (aps_pairs results), each pair rescored exactly from
+    the rows (host NumPy or device torch CSR); returns (aps_pairs of dot >= t, union size)."""
+    lib = load()
+    arr = (aps_pairs * max(len(lists), 1))()
+    for k, p in enumerate(lists):
+        arr[k] = p
+    (ip, ix, vv), f, keep = _csr_args(indptr, idx, val)
+    out = aps_pairs()
+    nc = _i64(0)
+    _check(lib.aps_pairs_verify(arr, len(lists), ip, ix, vv, int(n), int(m), float(t), flags | f,
+                                _stream_ptr(stream), ctypes.byref(out), ctypes.byref(nc)), "aps_pairs_verify")
+    del keep
+    return out, int(nc.value)
 

@@ -512,4 +512,28 @@ aps_status aps_graph_copy_to(const aps_graph *g, int64_t *row_ptr, int32_t *col,
 
 void aps_graph_free(aps_graph *g) { graph_release(g); }
 
+aps_status aps_pairs_verify(const aps_pairs *lists, int32_t k, const int64_t *indptr, const int32_t *idx,
+                            const float *val, int32_t n, int32_t m, float t, uint32_t flags, void *stream,
+                            aps_pairs *out, int64_t *n_candidates) {
+    if (!out || (k > 0 && !lists) || k < 0 || n < 0 || m < 1) {
+        set_error("need out != NULL, k >= 0 lists, n >= 0 and m >= 1");
+        return APS_EINVAL;
+    }
+    if (!(t > 0.f) || !(t <= 1.f)) {
+        set_error("threshold t must be in (0, 1], got %g", (double)t);
+        return APS_EINVAL;
+    }
+    memset(out, 0, sizeof(*out));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    HostCsrCopy hc;
+    const int64_t *dp = nullptr;
+    const int32_t *di = nullptr;
+    const float *dv = nullptr;
+    APS_TRY(stage_csr(indptr, idx, val, n, flags, s, hc, &dp, &di, &dv));
+    aps_status st = pairs_verify(lists, k, dp, di, dv, n, m, t, s, out, n_candidates);
+    if (st == APS_OK && (flags & APS_HOST_OUTPUT)) st = pairs_to_host(out, s);
+    if (st != APS_OK) pairs_release(out);
+    return st;
+}
+
 }  // extern "C"

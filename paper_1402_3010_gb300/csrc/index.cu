@@ -78,7 +78,7 @@ __global__ void k_validate(const int64_t *__restrict__ indptr, const int32_t *__
                     best = fmaxf(best, v);
                 }
             } else {
-                if (fabs(nrm - 1.0) > 1e-3) code = E_NORM;
+                if ((flags & APS_SUBUNIT_NORMS) ? nrm > 1.0 + 1e-3 : fabs(nrm - 1.0) > 1e-3) code = E_NORM;
                 for (int64_t p = a; p < b; p++) {
                     vout[p] = val[p];
                     best = fmaxf(best, val[p]);
@@ -289,7 +289,8 @@ const char *code_name(int c) {
         case E_IDX_RANGE: return "dimension index out of [0, m)";
         case E_IDX_ORDER: return "dimension indices not strictly increasing";
         case E_VALUE: return "value not finite and > 0";
-        case E_NORM: return "row L2 norm differs from 1 by more than 1e-3 (pass APS_NORMALIZE)";
+        case E_NORM: return "row L2 norm differs from 1 by more than 1e-3 (pass APS_NORMALIZE), or exceeds 1 + 1e-3 "
+                            "with APS_SUBUNIT_NORMS";
         default: return "invalid input";
     }
 }

@@ -74,27 +74,6 @@ struct IndexArrays {
     DBuf<int2> post;
 };
 
-// The self-join of a single-instance index with every buffer carved out of `arena`
-// (arena_bytes, 256-byte aligned) and at most max_ctas CTAs; pairs land in the caller's
-// arrays (capacity cap). *count receives the number of pairs, also on APS_EOVERFLOW.
-aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes, int max_ctas, int32_t *oi,
-                        int32_t *oj, float *os, int64_t cap, int64_t *count, cudaStream_t s);
-
-// Dense all-pairs of X[n, d] (float32 rows; host or device per APS_DEVICE_PTRS) on the
-// tensor cores with exact rescoring; d % 64 == 0, 64 <= d <= 512.
-aps_status dense_all_pairs(const float *X, int32_t n, int32_t d, float t, uint32_t flags, cudaStream_t s,
-                           aps_pairs *out, aps_stats *stats);
-aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t, cudaStream_t s, aps_pairs *out,
-                                  aps_stats *stats);
-double dense_margin(int d);
-
-// The similarity graph G_S as a CSR adjacency from a pair list, its k nearest neighbours,
-// and its release (graph.cu).
-aps_status graph_csr(const int32_t *i, const int32_t *j, const float *s, int64_t count, int32_t n, uint32_t flags,
-                     cudaStream_t st, aps_graph *out);
-aps_status graph_knn(const aps_graph *g, int32_t k, int32_t *nbr, float *wk, uint32_t flags, cudaStream_t s);
-void graph_release(aps_graph *g);
-
 }  // namespace aps
 
 struct aps_index {
@@ -184,5 +163,10 @@ aps_status graph_csr(const int32_t *i, const int32_t *j, const float *s, int64_t
                      cudaStream_t st, aps_graph *out);
 aps_status graph_knn(const aps_graph *g, int32_t k, int32_t *nbr, float *wk, uint32_t flags, cudaStream_t s);
 void graph_release(aps_graph *g);
+
+// Union of candidate pair lists, exact float64 rescoring from the rows, pairs >= t (verify.cu).
+aps_status pairs_verify(const aps_pairs *lists, int32_t k, const int64_t *indptr, const int32_t *idx,
+                        const float *val, int32_t n, int32_t m, float t, cudaStream_t s, aps_pairs *out,
+                        int64_t *n_candidates);
 
 }  // namespace aps
