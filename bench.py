@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--n", type=int, default=200_000)
     ap.add_argument("--m", type=int, default=100_000)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-sample", type=int, default=600, help="queries in the oracle's timed sample")
+    ap.add_argument("--cpu-sample", type=int, default=600, help="queries per core in the oracle's timed sample")
+    ap.add_argument("--cpu-cores", type=int, default=0, help="host cores for the CPU baseline (0: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="sparse", choices=["sparse", "dense", "batched", "serving", "ablation", "graph", "horizontal", "vertical"],
                     help="sparse: the 200k-vector sparse self-join (default line); dense: the 200k x 256 "
@@ -156,6 +157,51 @@ def cpu_baseline(c, t, sample):
         "sample": f"sequential all-pairs-2 (C, FP64) over the full n={c.n} index build, Find-Matches for "
                   f"{int(mask.sum())} random queries ({cnt['evaluations']} evaluations) in {dt:.2f} s",
         "seconds": dt,
+    }
+
+
+def _oracle_worker(job):
+    """One host core's share of the CPU baseline (a spawned process): the oracle's
+    all-pairs-2 over the full index build with Find-Matches for k random queries."""
+    n, m, t, k, seed = job
+    sys.path.insert(0, ROOT)
+    import oracle
+
+    c = workload(n, m)
+    rng = np.random.default_rng(seed)
+    mask = np.zeros(c.n, np.uint8)
+    mask[rng.choice(c.n, size=min(k, c.n), replace=False)] = 1
+    t0 = time.perf_counter()
+    _, cnt = oracle.all_pairs(c, float(np.float32(t)), oracle.ALL_PAIRS_2, query_mask=mask)
+    return cnt["evaluations"], time.perf_counter() - t0
+
+
+def host_cores(args) -> int:
+    return args.cpu_cores if args.cpu_cores > 0 else (os.cpu_count() or 1)
+
+
+def cpu_baseline_cores(c, t, per_core: int, cores: int):
+    """The oracle on every host core at once (the horizontal idea of Sec. 5.2 on the CPU:
+    each core runs the sequential program on its own random queries): value = all cores'
+    evaluations / the slowest core's time. A spawned pool (no CUDA state is inherited)."""
+    import multiprocessing as mp
+
+    if cores <= 1:
+        return cpu_baseline(c, t, per_core)
+    jobs = [(c.n, c.m, t, per_core, 1000 + k) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    evals = sum(r[0] for r in res)
+    secs = max(r[1] for r in res)
+    return {
+        "value": evals / secs,
+        "unit": UNIT,
+        "cores": cores,
+        "kind": "oracle",
+        "sample": f"sequential all-pairs-2 (C, FP64) on each of {cores} host cores at once: each builds the full "
+                  f"n={c.n} index and runs Find-Matches for {per_core} random queries ({evals} evaluations in all); "
+                  f"slowest core {secs:.2f} s",
+        "seconds": secs,
     }
 
 
@@ -323,12 +369,13 @@ def run_aps(args, rank, world):
         "phases_ms": {"build": last["ms_build"], "join": last["ms_join"], "output": last["ms_sort"],
                       "join_call": last["ms_total"]},
         "work": {k: last[k] for k in ("visits", "candidates", "verified", "pairs", "band")},
+        "rates_per_s_of_join": {k: last[k] / (jm * 1e-3) for k in ("visits", "candidates", "pairs")},
         "gpu_launches": launches,
         "e2e": e2e,
         "clocks": clk,
     }
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(c, t, args.cpu_sample)
+        line["cpu_baseline"] = cpu_baseline_cores(c, t, args.cpu_sample, host_cores(args))
     return line
 
 
@@ -634,12 +681,13 @@ def run_reference(args, rank):
         return None
     t = float(np.float32(args.t))
     c = workload(args.n, args.m)
-    evals, secs = 0, 0.0
+    secs = 0.0
+    cores = host_cores(args)
     for _ in range(max(args.warmup, 0)):
-        cpu_baseline(c, t, max(args.cpu_sample // 8, 10))
+        cpu_baseline_cores(c, t, max(args.cpu_sample // 8, 10), cores)
     res = []
     for _ in range(args.steps):
-        r = cpu_baseline(c, t, args.cpu_sample)
+        r = cpu_baseline_cores(c, t, args.cpu_sample, cores)
         res.append(r)
         secs += r["seconds"]
     value = statistics.mean(r["value"] for r in res)
@@ -658,8 +706,8 @@ def run_reference(args, rank):
         "dtype": "f64",
         "data": "synthetic (seeded generator, no dataset)",
         "config": {"workload": WORKLOAD, "n": c.n, "m": c.m, "nnz": c.nnz, "t": t,
-                   "parallelism": "CPU, 1 thread"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": res[-1]["sample"]},
+                   "parallelism": f"CPU, {cores} host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": res[-1]["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
