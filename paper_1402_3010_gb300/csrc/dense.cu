@@ -464,35 +464,72 @@ __global__ void k_to_bf16(const float *__restrict__ X, int64_t n, int d, int64_t
         Xb[e] = (e < n * d) ? __float2bfloat16_rn(X[e]) : __float2bfloat16_rn(0.f);
 }
 
-// One warp per candidate (sorted keys i*n + j): float32 dot from X with a tree reduction;
-// float64 when the float32 score lies within the band of t.
+// Exact rescoring of the candidates (sorted keys i*n + j). Each warp takes a contiguous run
+// of candidates and scores four at a time, issuing all their row loads (float4) before any
+// arithmetic, so that four pairs' reads are in flight per warp; consecutive candidates share
+// row i, which then comes from L1. float32 dot with a tree reduction; float64 when the
+// float32 score lies within the band of t. X is 16-byte aligned and d % 64 == 0, d <= 512.
+constexpr int RS_BATCH = 4;
+
 __global__ void k_rescore(const unsigned long long *__restrict__ keys, int64_t nc, const float *__restrict__ X, int n,
                           int d, float t, float beta, int32_t *keep, float *score, unsigned long long *nband) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = wid; c < nc; c += nw) {
-        const unsigned long long k = keys[c];
-        const int64_t i = (int64_t)(k / (unsigned long long)n), j = (int64_t)(k % (unsigned long long)n);
-        const float *xi = X + i * d, *xj = X + j * d;
-        float acc = 0.f;
-        for (int e = lane; e < d; e += 32) acc = fmaf(xi[e], xj[e], acc);
+    const int64_t per = (nc + nw - 1) / nw;
+    const int64_t c0 = wid * per, c1 = min(nc, c0 + per);
+    const int d4 = d >> 2;
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    for (int64_t c = c0; c < c1; c += RS_BATCH) {
+        int64_t ii[RS_BATCH], jj[RS_BATCH];
+        float acc[RS_BATCH];
 #pragma unroll
-        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        float s = acc;
-        bool in = s >= t;
-        if (fabsf(s - t) <= beta) {
-            double a64 = 0.0;
-            for (int e = lane; e < d; e += 32) a64 += (double)xi[e] * (double)xj[e];
-#pragma unroll
-            for (int o = 16; o; o >>= 1) a64 += __shfl_xor_sync(0xffffffffu, a64, o);
-            in = a64 >= (double)t;
-            s = (float)a64;
-            if (lane == 0) atomicAdd(nband, 1ull);
+        for (int u = 0; u < RS_BATCH; u++) {
+            const unsigned long long k = keys[min(c + u, c1 - 1)];
+            ii[u] = (int64_t)(k / (unsigned long long)n);
+            jj[u] = (int64_t)(k % (unsigned long long)n);
+            acc[u] = 0.f;
         }
-        if (lane == 0) {
-            keep[c] = in ? 1 : 0;
-            score[c] = s;
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            if (lane + 32 * v < d4) {
+                float4 a[RS_BATCH], b[RS_BATCH];
+#pragma unroll
+                for (int u = 0; u < RS_BATCH; u++) {
+                    a[u] = X4[ii[u] * d4 + lane + 32 * v];
+                    b[u] = X4[jj[u] * d4 + lane + 32 * v];
+                }
+#pragma unroll
+                for (int u = 0; u < RS_BATCH; u++) {
+                    acc[u] = fmaf(a[u].x, b[u].x, acc[u]);
+                    acc[u] = fmaf(a[u].y, b[u].y, acc[u]);
+                    acc[u] = fmaf(a[u].z, b[u].z, acc[u]);
+                    acc[u] = fmaf(a[u].w, b[u].w, acc[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < RS_BATCH; u++) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+        }
+        for (int u = 0; u < RS_BATCH && c + u < c1; u++) {
+            float s = acc[u];
+            bool in = s >= t;
+            if (fabsf(s - t) <= beta) {
+                const float *xi = X + ii[u] * d, *xj = X + jj[u] * d;
+                double a64 = 0.0;
+                for (int e = lane; e < d; e += 32) a64 += (double)xi[e] * (double)xj[e];
+#pragma unroll
+                for (int o = 16; o; o >>= 1) a64 += __shfl_xor_sync(0xffffffffu, a64, o);
+                in = a64 >= (double)t;
+                s = (float)a64;
+                if (lane == 0) atomicAdd(nband, 1ull);
+            }
+            if (lane == 0) {
+                keep[c + u] = in ? 1 : 0;
+                score[c + u] = s;
+            }
         }
     }
 }
@@ -746,9 +783,9 @@ aps_status dense_all_pairs(const float *X, int32_t n, int32_t d, float t, uint32
                            aps_pairs *out, aps_stats *stats) {
     DBuf<float> dx, dy;
     const float *Xd = X;
-    if (!(flags & APS_DEVICE_PTRS)) {
+    if (!(flags & APS_DEVICE_PTRS) || (reinterpret_cast<uintptr_t>(X) & 15)) {  // host, or not 16-byte aligned
         APS_TRY(dx.alloc((size_t)n * d, s));
-        if ((int64_t)n * d) APS_CUDA(cudaMemcpyAsync(dx.p, X, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, s));
+        if ((int64_t)n * d) APS_CUDA(cudaMemcpyAsync(dx.p, X, sizeof(float) * (size_t)n * d, cudaMemcpyDefault, s));
         Xd = dx.p;
     }
     DBuf<unsigned long long> bad;

@@ -120,3 +120,23 @@ def test_dense_full_size_sampled_rows(aps):
     common = np.intersect1d(gk, rk)
     err = max(abs(smap[k] - rmap[k]) for k in common.tolist())
     assert err <= 1e-5
+
+
+def test_dense_misaligned_device_rows(aps):
+    """A device X that is not 16-byte aligned (a view one float into a buffer) gives the
+    same pairs."""
+    import torch
+
+    X = synth.dense_mixture(1000, 128, 20, 0.15, seed=12)
+    t = 0.8
+    buf = torch.empty(X.size + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = torch.from_numpy(X.ravel()).cuda()
+    Xm = buf[1:].view(X.shape)
+    assert Xm.data_ptr() % 16 != 0
+    p, _ = aps.aps_all_pairs_dense(Xm, t)
+    try:
+        i, j, s = aps.pairs_to_numpy(p)
+    finally:
+        aps.aps_pairs_free(p)
+    compare(i, j, s, oracle.dense_all_pairs(X, f32(t)), f32(t), 1000)
+
