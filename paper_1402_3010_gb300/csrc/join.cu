@@ -7,17 +7,19 @@
 // because n floats do not fit on chip). For a query x (a whole vector of the set, taken
 // from a cost-ordered work list) and each window of candidates y > x:
 //   1. accumulate: A[y] += x[i] * y[i] over the posting lists of x's components,
-//      first over the components with remscore >= t (these may create candidates),
-//      then over the rest, which only update candidates that exist (remscore);
-//      entries with |y| below minsize are skipped using the size class stored in the
-//      entry. Lists are in id order, so a warp's 32 lanes add into 32 increasing slots;
-//   2. verify: the non-zero slots are compacted into a per-warp ring so that every lane
-//      takes one candidate; the upperbound test
-//      A[y] + min(|y'|, |x|) * maxweight(x) * maxweight(y') >= t, then
+//      first over the components with remscore >= t (these may create candidates, and
+//      mark each touched slot in a bitmap), then over the rest, which only update
+//      candidates that exist (remscore); entries with |y| below minsize are skipped using
+//      the size class stored in the entry. Lists are in id order, so a warp's 32 lanes add
+//      into 32 increasing slots;
+//   2. verify: each warp walks its share of the bitmap and takes the marked slots in
+//      order, one candidate per lane: A[y] + ||y'||_2 < t rejects cheaply, then the
+//      upperbound test A[y] + min(|y'|, |x|) * maxweight(x) * maxweight(y') >= t, then
 //      s = A[y] + dot(x, y') with y' the unindexed prefix of y; scores within a band of
 //      t are recomputed in float64 and decided there;
-//   3. compact: warp ballots give each emitted pair its slot; one global reservation
-//      per (x, window); pairs land in a staging buffer as (y, score) in increasing y.
+//   3. compact: warp ballots give each emitted pair its slot; the window's run comes from
+//      a staging slab the group reserves in bulk; pairs land as (y, score) in increasing
+//      y and the run is recorded at its (x, window) slot.
 // The output stage scans the per-(x, window) counts and gathers the staged runs into
 // (i, j, score) arrays, which are then in (i, j) order without a sort.
 #include <algorithm>
