@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                 const bool ph0 = cp < ncreate;
                 if (cp < xl) {
                     const int c = ph0 ? qs + cp : cp - ncreate;
-                    const int2 e = xrow[c];
+                    const int2 e = c < xs ? xr[c] : xrow[c];  // x's row from shared memory when held there
                     const int64_t R = (int64_t)I.rbase + e.x;
                     xv = __int_as_float(e.y);
                     int64_t ls = P.lptr[R], le = P.lptr[R + 1];
