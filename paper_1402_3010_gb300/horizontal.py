@@ -10,7 +10,8 @@ processing order. The paper moves size(V)·(p-1) vector elements for the exchang
 this driver (each rank reads every lower rank's part).
 
 Ranks exchange parts and results through a key-value store (``torch.distributed.TCPStore``
-or anything with ``set``/``get``/``wait``), which also carries failure detection: the
+or anything with ``set``/``get``/``wait``; values are pickled, so the store must be private
+to the job's own processes), which also carries failure detection: the
 collecting rank waits for each rank's result with a timeout; a rank that never delivers
 is declared failed, and its share is recomputed by the collector from the partition
 (re-read through ``part_of``). Failures are host-side only (an exception or an exit
