@@ -115,6 +115,8 @@ def _distinct_zipf_rows_chunk(rng, lengths, m, s):
     acc_row = np.zeros(0, dtype=np.int64)
     acc_rank = np.zeros(0, dtype=np.int64)
     acc_ord = np.zeros(0, dtype=np.int64)
+    done_row, done_rank, done_ord = [], [], []  # rows that already hold all their ranks
+    frozen = np.zeros(n, dtype=bool)
     have = np.zeros(n, dtype=np.int64)
     draw_base = 0
     for _round in range(64):
@@ -152,11 +154,23 @@ def _distinct_zipf_rows_chunk(rng, lengths, m, s):
         starts = np.searchsorted(r_k, np.arange(n), side="left")
         pos = np.arange(r_k.size) - starts[r_k]
         sel = pos < lengths[r_k]
-        acc_row, acc_rank, acc_ord = r_k[sel], k_k[sel], o_k[sel]
-        have = np.bincount(acc_row, minlength=n).astype(np.int64)
+        r_k, k_k, o_k = r_k[sel], k_k[sel], o_k[sel]
+        got = np.bincount(r_k, minlength=n).astype(np.int64)
+        # rows that are complete leave the working set (their selection is final)
+        fin = got[r_k] == lengths[r_k]
+        done_row.append(r_k[fin])
+        done_rank.append(k_k[fin])
+        done_ord.append(o_k[fin])
+        acc_row, acc_rank, acc_ord = r_k[~fin], k_k[~fin], o_k[~fin]
+        frozen[r_k[fin]] = True
+        have = np.where(frozen, lengths, got)
     else:  # pragma: no cover - 64 rounds always suffice for the shapes used here
         raise RuntimeError("distinct Zipf sampling did not converge")
-    return acc_row, acc_rank
+    out_row = np.concatenate(done_row + [acc_row])
+    out_rank = np.concatenate(done_rank + [acc_rank])
+    out_ord = np.concatenate(done_ord + [acc_ord])
+    o = np.lexsort((out_ord, out_row))  # by row, then draw order
+    return out_row[o], out_rank[o]
 
 
 def sparse_vectors(
