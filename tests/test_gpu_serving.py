@@ -189,3 +189,24 @@ def test_serving_cancel_budget_and_errors(aps):
             A.aps_server_free(sv)
     finally:
         A.aps_index_free(h)
+
+
+def test_serving_shape_index_sampled_queries(aps):
+    """The serving workload's generator (power law, mean 40, shared dense dimensions) with
+    a 200k-vector queryable index at t = 0.75: 64 queries from the query generator against
+    the oracle's float64 query-vs-set brute force."""
+    import torch
+
+    import paper_1402_3010_gb300 as A
+
+    c, t = synth.config_serving(n=200_000)
+    q = synth.serving_queries(64)
+    dev = [torch.from_numpy(a).cuda() for a in (c.indptr, c.idx, c.val)]
+    h = A.aps_build_index(*dev, c.n, c.m, t, A.QUERYABLE)
+    try:
+        i, j, s = query(aps, h, q, t)
+    finally:
+        A.aps_index_free(h)
+    ref = oracle.bruteforce_cross(q, c, f32(t))
+    r = compare(i, j, s, ref, f32(t), c.n, self_join=False)
+    assert r["pairs"] > 0

@@ -414,3 +414,65 @@ def test_batched_concatenated_csr_matches_per_instance_oracle(aps):
     finally:
         for o in outs:
             A.aps_pairs_free(o)
+
+
+def test_full_size_200k_sampled_rows(aps):
+    """The 200k x 100k power-law workload at t = 0.7 in the bench's configuration (device
+    CSR, default flags): 40 sampled vectors' pairs checked one by one against the oracle's
+    float64 brute force over the whole set, plus the global form of the result."""
+    import torch
+
+    c = synth.config_large()
+    t = f32(0.7)
+    dev = [torch.from_numpy(a).cuda() for a in (c.indptr, c.idx, c.val)]
+    h = aps.aps_build_index(*dev, c.n, c.m, t)
+    try:
+        p = aps.aps_all_pairs(h)
+        try:
+            i, j, s = aps.pairs_to_numpy(p)
+        finally:
+            aps.aps_pairs_free(p)
+        st = aps.aps_index_stats(h)
+    finally:
+        aps.aps_index_free(h)
+    keys = i.astype(np.int64) * c.n + j
+    assert len(i) == st["pairs"] > 10_000_000
+    assert np.all(np.diff(keys) > 0) and np.all(i < j)
+    rows = np.random.default_rng(3).choice(c.n, 40, replace=False)
+    ref = oracle.bruteforce_rows(c, t, rows)
+    sel = np.isin(i, rows) | np.isin(j, rows)
+    rk = ref.keys(c.n)
+    rmap = dict(zip(rk.tolist(), ref.s.tolist()))
+    gmap = dict(zip(keys[sel].tolist(), s[sel].tolist()))
+    assert len(rmap) > 0
+    for k in set(rmap) - set(gmap):  # only pairs inside the 1e-5 band may differ
+        assert abs(rmap[k] - t) <= 1e-5
+    for k in set(gmap) - set(rmap):
+        assert abs(gmap[k] - t) <= 1e-5
+    common = set(gmap) & set(rmap)
+    assert max(abs(gmap[k] - rmap[k]) for k in common) <= 1e-5
+
+
+def test_batched_workload_shape_sampled_instances(aps):
+    """The batched workload's generator and thresholds (64 of its instances, concatenated
+    CSR, one call): 6 sampled instances against the oracle's brute force."""
+    import torch
+
+    import paper_1402_3010_gb300 as A
+
+    ro, c, m, ts = synth.config_batched_csr(k=64)
+    dev = [torch.from_numpy(a).cuda() for a in (c.indptr, c.idx, c.val)]
+    outs, st = A.aps_batch_all_pairs_csr(ro, *dev, m, ts)
+    try:
+        assert sum(int(o.count) for o in outs) == st["pairs"]
+        sizes = np.diff(ro)
+        pick = np.argsort(sizes)[[0, 10, 30, 45, 55, 60]]
+        for r in pick.tolist():
+            a, b = int(ro[r]), int(ro[r + 1])
+            ip = c.indptr[a:b + 1] - c.indptr[a]
+            cr = synth.SparseCSR(ip, c.idx[c.indptr[a]:c.indptr[b]], c.val[c.indptr[a]:c.indptr[b]], b - a, int(m[r]))
+            i, j, s = A.pairs_to_numpy(outs[r])
+            compare(i, j, s, oracle.bruteforce(cr, float(ts[r])), float(ts[r]), max(b - a, 1), csr=cr)
+    finally:
+        for o in outs:
+            A.aps_pairs_free(o)
