@@ -205,6 +205,23 @@ def cpu_baseline_cores(c, t, per_core: int, cores: int):
     }
 
 
+def max_over_ranks(ms: float, dev, world: int) -> float:
+    """The slowest rank's time: the job's time for replicas that each did the same work."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_value(evals_per_replica: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job evaluations/s: every replica's evaluations over the slowest rank's time."""
+    return world * evals_per_replica * steps / (ms * 1e-3)
+
+
 def measured_traffic(profile: str, source: str, t: float):
     """DRAM bytes per launch from a committed ncu capture (profiles/<profile>), valid only
     while the kernel source is byte-identical to the one the counters were taken from."""
@@ -285,12 +302,7 @@ def run_aps(args, rank, world):
     launches = aps.aps_launch_count() - l0
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dev, world)
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -319,6 +331,7 @@ def run_aps(args, rank, world):
         outs = [e2e_step() for _ in range(args.e2e_steps)]
         barrier()
         dt = time.perf_counter() - t0
+        dt = max_over_ranks(dt * 1e3, dev, world) * 1e-3  # the slowest rank's end-to-end time
         e2e = {"value": world * evals * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": hbytes,
                "d2h_bytes_per_step": int(max(outs)) * 12, "ms_per_step": 1000 * dt / args.e2e_steps}
 
@@ -335,7 +348,7 @@ def run_aps(args, rank, world):
     traffic = measured_traffic("join_kernel_traffic.json", "join.cu", t) if (c.n, c.m) == (200_000, 100_000) else None
     line = {
         "metric": METRIC,
-        "value": world * evals * args.steps / (ms * 1e-3),
+        "value": replica_value(evals, args.steps, world, ms),
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
@@ -435,12 +448,7 @@ def run_dense(args, rank, world):
     launches = aps.aps_launch_count() - l0
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dev, world)
     e2e = None
     if args.e2e_steps > 0:
         hX = torch.from_numpy(X).pin_memory()
@@ -462,6 +470,7 @@ def run_dense(args, rank, world):
         outs = [e2e_step() for _ in range(args.e2e_steps)]
         barrier()
         dt = time.perf_counter() - t0
+        dt = max_over_ranks(dt * 1e3, dev, world) * 1e-3
         e2e = {"value": world * evals * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": X.nbytes,
                "d2h_bytes_per_step": int(max(outs)) * 12, "ms_per_step": 1000 * dt / args.e2e_steps}
     if rank != 0:
@@ -471,7 +480,7 @@ def run_dense(args, rank, world):
     gm = statistics.mean(gemm_ms)
     achieved = flops / (gm * 1e-3) / 1e12
     line = {
-        "metric": METRIC, "value": world * evals * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": replica_value(evals, args.steps, world, ms), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic (seeded generator, no dataset)",
