@@ -201,11 +201,10 @@ __global__ void k_post_keys(const int64_t *__restrict__ cptr, const int32_t *__r
     }
 }
 
-__global__ void k_post_fill(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                            const int32_t *__restrict__ erow, const float *__restrict__ cval,
-                            const int32_t *__restrict__ len, const int32_t *__restrict__ vinst,
-                            const InstDesc *__restrict__ inst, int64_t nsuf, int2 *post, int32_t *lcount,
-                            int32_t *wcount) {
+__global__ void k_post_fill(const uint32_t *__restrict__ vals, const int32_t *__restrict__ erow,
+                            const float *__restrict__ cval, const int32_t *__restrict__ len,
+                            const int32_t *__restrict__ vinst, const InstDesc *__restrict__ inst, int64_t nsuf,
+                            int2 *post) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nsuf; q += (int64_t)gridDim.x * blockDim.x) {
         uint32_t p = vals[q];
         int64_t x = erow[p];
@@ -213,9 +212,19 @@ __global__ void k_post_fill(const uint64_t *__restrict__ keys, const uint32_t *_
         const int32_t lid = (int32_t)(x - I.vbase);
         const int32_t tag = I.packed ? (min(len[x], 255) << 24) : 0;
         post[q] = make_int2(lid | tag, __float_as_int(cval[p]));
-        int64_t R = (int64_t)keys[q];
-        atomicAdd(&lcount[R], 1);
-        if (I.nw > 1) atomicAdd(&wcount[I.wbase + (R - I.rbase) * (I.nw + 1) + lid / I.W], 1);
+    }
+}
+
+// List pointers from the sorted posting keys: lptr[R] = first suffix entry with key >= R
+// (binary search; lptr[M] = nsuf).
+__global__ void k_lptr(const uint64_t *__restrict__ keys, int64_t nsuf, int64_t M, int64_t *lptr) {
+    for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R <= M; R += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nsuf;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (keys[mid] < (uint64_t)R) lo = mid + 1; else hi = mid;
+        }
+        lptr[R] = lo;
     }
 }
 
@@ -231,18 +240,25 @@ __global__ void k_pack(const int64_t *__restrict__ cptr, const int32_t *__restri
         vmeta[x] = make_int4((int32_t)cptr[x], len[x], split[x], __float_as_int(mwpre[x]));
 }
 
-// Window offsets inside each list of a multi-window instance: in-place exclusive scan of
-// the per-window counts of one rank.
-__global__ void k_wptr_scan(const InstDesc *__restrict__ inst, int k, int64_t M, int32_t *wptr) {
+// Window offsets inside each list of a multi-window instance: w[i] = the offset in list R
+// of its first entry with local id >= i * W (lists are in increasing id; binary search).
+__global__ void k_wptr(const InstDesc *__restrict__ inst, int k, int64_t M, const int64_t *__restrict__ lptr,
+                       const int2 *__restrict__ post, int32_t *wptr) {
     for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R < M; R += (int64_t)gridDim.x * blockDim.x) {
         const InstDesc &I = inst[inst_of_rank(inst, k, R)];
         if (I.nw <= 1) continue;
+        const int32_t idmask = I.packed ? 0x00ffffff : 0x7fffffff;
+        const int64_t a = lptr[R], b = lptr[R + 1];
         int32_t *w = wptr + I.wbase + (R - I.rbase) * (I.nw + 1);
-        int32_t acc = 0;
+        int64_t lo = a;
         for (int i = 0; i <= I.nw; i++) {
-            int32_t c = w[i];
-            w[i] = acc;
-            acc += c;
+            const int32_t bound = i * I.W;
+            int64_t hi = b;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if ((post[mid].x & idmask) < bound) lo = mid + 1; else hi = mid;
+            }
+            w[i] = (int32_t)(lo - a);
         }
     }
 }
@@ -457,11 +473,8 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     {
         DBuf<uint64_t> keys;
         DBuf<uint32_t> vals;
-        DBuf<int32_t> lcount;
         APS_TRY(keys.alloc((size_t)nnz, s));
         APS_TRY(vals.alloc((size_t)nnz, s));
-        APS_TRY(lcount.alloc((size_t)M, s));
-        APS_CUDA(cudaMemsetAsync(lcount.p, 0, sizeof(int32_t) * M, s));
         unsigned long long *nsuf_d = err.p + 1;
         if (nnz > 0) {
             k_post_keys<<<gE, T256, 0, s>>>(d.cptr.p, d.crank.p, erow.p, d.split.p, d.vinst.p, d.inst.p, nnz, M,
@@ -477,14 +490,14 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
         APS_TRY(d.wptr.alloc((size_t)std::max<int64_t>(nwptr, 1), s));
         if (nwptr) APS_CUDA(cudaMemsetAsync(d.wptr.p, 0, sizeof(int32_t) * nwptr, s));
         if (ix->nsuf > 0) {
-            k_post_fill<<<grid_for(ix->nsuf, T256), T256, 0, s>>>(keys.p, vals.p, erow.p, d.cval.p, d.len.p,
-                                                                  d.vinst.p, d.inst.p, ix->nsuf, d.post.p, lcount.p,
-                                                                  d.wptr.p);
+            k_post_fill<<<grid_for(ix->nsuf, T256), T256, 0, s>>>(vals.p, erow.p, d.cval.p, d.len.p, d.vinst.p,
+                                                                  d.inst.p, ix->nsuf, d.post.p);
             APS_LAUNCH_CHECK();
         }
-        APS_TRY(scan_exclusive(lcount.p, d.lptr.p, M, s));
+        k_lptr<<<grid_for(M + 1, T256), T256, 0, s>>>(keys.p, ix->nsuf, M, d.lptr.p);
+        APS_LAUNCH_CHECK();
         if (nwptr) {
-            k_wptr_scan<<<gM, T256, 0, s>>>(d.inst.p, k, M, d.wptr.p);
+            k_wptr<<<gM, T256, 0, s>>>(d.inst.p, k, M, d.lptr.p, d.post.p, d.wptr.p);
             APS_LAUNCH_CHECK();
         }
         APS_TRY(d.crow.alloc((size_t)std::max<int64_t>(nnz, 1), s));
