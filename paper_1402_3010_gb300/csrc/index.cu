@@ -162,20 +162,40 @@ __global__ void k_split(const int64_t *__restrict__ cptr, const int32_t *__restr
         int32_t L = (int32_t)(b - a);
         int32_t qs = L, cs = L;
         double bmw = 0.0, ss = 0.0;
-        for (int64_t p = a; p < b; p++) {
-            double v = (double)cval[p];
-            bmw += v * (double)mwr[(int64_t)I.rbase + crank[p]];
-            ss += v * v;
-            if (qs == L && bmw >= t) qs = (int32_t)(p - a);
-            if (cs == L && ss * (1.0 + 2e-3) >= t * t) cs = (int32_t)(p - a);
-            if (qs < L && cs < L) break;
+        // four components' loads at a time; the sums still run in component order
+        bool stop = false;
+        for (int64_t p0 = a; p0 < b && !stop; p0 += 4) {
+            double v4[4], m4[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t p = min(p0 + u, b - 1);
+                v4[u] = (double)cval[p];
+                m4[u] = (double)mwr[(int64_t)I.rbase + crank[p]];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t p = p0 + u;
+                if (stop || p >= b) continue;
+                bmw += v4[u] * m4[u];
+                ss += v4[u] * v4[u];
+                if (qs == L && bmw >= t) qs = (int32_t)(p - a);
+                if (cs == L && ss * (1.0 + 2e-3) >= t * t) cs = (int32_t)(p - a);
+                if (qs < L && cs < L) stop = true;
+            }
         }
         int32_t sp = (flags & APS_NO_PARTIAL_INDEX) ? 0 : ((flags & APS_QUERYABLE) ? cs : qs);
         float best = 0.f;
         double pss = 0.0;
-        for (int64_t p = a; p < a + sp; p++) {
-            best = fmaxf(best, cval[p]);
-            pss += (double)cval[p] * (double)cval[p];
+        for (int64_t p0 = a; p0 < a + sp; p0 += 4) {
+            float c4[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) c4[u] = cval[min(p0 + u, a + sp - 1)];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (p0 + u >= a + sp) continue;
+                best = fmaxf(best, c4[u]);
+                pss += (double)c4[u] * (double)c4[u];
+            }
         }
         split[x] = sp;
         qsplit[x] = qs;
@@ -276,11 +296,18 @@ __global__ void k_item_keys(const int64_t *__restrict__ cptr, const int32_t *__r
         uint64_t key;
         if (lx < (int64_t)I.n - 1) {
             double later = (double)(I.n - 1 - lx);
-            double lists = 0.0;
-            for (int64_t p = cptr[x]; p < cptr[x + 1]; p++) {
-                int64_t R = (int64_t)I.rbase + crank[p];
-                lists += (double)(lptr[R + 1] - lptr[R]);
+            int64_t lsum = 0;  // total length of x's posting lists (four lookups at a time)
+            const int64_t a = cptr[x], b = cptr[x + 1];
+            for (int64_t p0 = a; p0 < b; p0 += 4) {
+                int64_t l4[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int64_t R = (int64_t)I.rbase + crank[min(p0 + u, b - 1)];
+                    l4[u] = p0 + u < b ? lptr[R + 1] - lptr[R] : 0;
+                }
+                lsum += l4[0] + l4[1] + l4[2] + l4[3];
             }
+            const double lists = (double)lsum;
             double cost = lists * later / (double)I.n + later / 8.0 + 32.0;
             uint64_t c = cost >= 4294967295.0 ? 0xffffffffull : (uint64_t)cost;
             int cls = I.G == 1 ? 0 : I.G == 2 ? 1 : I.G == 4 ? 2 : 3;
