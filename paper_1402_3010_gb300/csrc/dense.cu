@@ -624,6 +624,9 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
     for (int64_t a = 0; a < nb; a++)
         for (int64_t b = a; b < nb; b += UNIT_BLOCKS)
             units.push_back(make_int4((int)a, (int)b, (int)std::min<int64_t>(b + UNIT_BLOCKS, nb), 0));
+    // longest units first: the clusters take them round-robin, so the short tail units
+    // even out the finish
+    std::stable_sort(units.begin(), units.end(), [](const int4 &p, const int4 &q) { return p.z - p.y > q.z - q.y; });
     DBuf<int4> dunits;
     APS_TRY(dunits.alloc(units.size(), s));
     APS_CUDA(cudaMemcpyAsync(dunits.p, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, s));
