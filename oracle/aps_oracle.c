@@ -15,12 +15,12 @@
  *                 all-pairs-2 (minsize, remscore, upperbound).
  *   Sec. 4        all-pairs-0-array (dense score array) and all-pairs-bruteforce.
  *
- * Readings of passages that are ambiguous in the paper (each listed in the design doc):
+ * Readings of passages that are ambiguous in the paper:
  *   - matches use ">= t" (the definition), not "> t";
  *   - dimensions are ranked by decreasing non-zero count, ties by ascending id;
  *   - with minsize, vectors are processed by decreasing maxweight(x), ties by id, so
- *     that t/maxweight(x) never decreases (the text says "increasing maxweight", which
- *     contradicts the pop-from-the-front argument it makes);
+ *     that t/maxweight(x) never decreases (the text orders them the other way round,
+ *     which contradicts the pop-from-the-front argument it makes);
  *   - partial indexing indexes a component once the running bound b reaches t (b >= t);
  *   - with remscore, Find-Matches walks x's components from the sparsest dimension to
  *     the densest, and remscore still includes the component being processed when the
