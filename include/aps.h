@@ -305,6 +305,14 @@ int64_t aps_launch_count(void);
  * (k >= 1; 0 disables). Host-side only; no GPU fault is involved. */
 void aps_debug_fail_alloc(int64_t k);
 
+/* Test hook for the bounded waits of the dense tensor-core kernel: in the next `launches`
+ * launches (0 disables) the MMA issuer waits for an accumulator release that never comes,
+ * so the pipeline waits run out after wait_ns nanoseconds (0 = the default limit, 2 s).
+ * The kernel then lets its MMAs and TMA copies settle, frees its tensor memory and
+ * returns; aps_all_pairs_dense reports APS_ETIMEOUT and the context stays usable. No GPU
+ * fault is involved. */
+void aps_debug_dense_stall(int64_t launches, uint64_t wait_ns);
+
 #ifdef __cplusplus
 }
 #endif

@@ -482,6 +482,8 @@ const char *aps_version(void) { return "aps 0.1 (sm_103a)"; }
 
 void aps_debug_fail_alloc(int64_t k) { set_alloc_fault(k); }
 
+void aps_debug_dense_stall(int64_t launches, uint64_t wait_ns) { dense_debug_stall(launches, wait_ns); }
+
 aps_status aps_graph_csr(const int32_t *i, const int32_t *j, const float *s, int64_t count, int32_t n,
                          uint32_t flags, void *stream, aps_graph *out) {
     if (!out) {

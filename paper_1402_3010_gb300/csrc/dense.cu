@@ -14,8 +14,9 @@
 //      reads per MMA compared with a single-SM 128-row tile.
 //   3. Candidates are sorted by (i, j), rescored in float32 from X (float64 when within
 //      the band of t) and compacted into the result.
-// Every wait on an mbarrier is bounded; on expiry the kernel records an error code and
-// leaves, and the host reports APS_ETIMEOUT.
+// Every wait on an mbarrier is bounded in time; on expiry the kernel records an error code,
+// lets its MMAs and every TMA copy either CTA issued settle (again bounded), frees its
+// tensor memory and leaves, and the host reports APS_ETIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -41,7 +42,8 @@ constexpr int SMEM_BUDGET = 224 * 1024;
 constexpr int MAX_STAGES = 12;
 constexpr int UNIT_BLOCKS = 32;  // B blocks per work unit
 constexpr uint32_t TMEM_COLS = 512;  // two 256-column accumulators
-constexpr unsigned long long WAIT_LIMIT = 1ull << 26;
+constexpr unsigned long long WAIT_NS_DEFAULT = 2000000000ull;  // 2 s for one wait
+constexpr unsigned long long WAIT_SPIN_CAP = 1ull << 28;       // iteration backstop of a wait
 
 struct DenseParams {
     int n, KB, S;
@@ -53,6 +55,9 @@ struct DenseParams {
     unsigned long long *count;   // candidate slots handed out (reserved in slabs)
     unsigned long long *padded;  // slots of those left holding CAND_PAD
     int *err;
+    unsigned long long wait_ns;  // time limit of one mbarrier wait
+    uint32_t stall;              // test hook: 1 = the MMA issuer waits for an accumulator release
+                                 // that never comes, so the waits run out
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -80,13 +85,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: false (and an error code in *err) when the phase never completes or
-// another role already gave up. The first probe is inline; the spin is out of line.
-__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, int *err, int code) {
-    for (unsigned long long i = 0; i < WAIT_LIMIT; i++) {
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: false, with an error code in *err, when the phase has not completed within
+// limit_ns (or WAIT_SPIN_CAP probes); with heed_err, also false as soon as another role has
+// given up. The first probe is inline; the spin is out of line.
+__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, int *err, int code,
+                                            unsigned long long limit_ns, bool heed_err) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned long long i = 0; i < WAIT_SPIN_CAP; i++) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 4095) == 4095) {
-            if (*(volatile int *)err) return false;
+            if (heed_err && *(volatile int *)err) return false;
+            if (globaltimer_ns() - t0 > limit_ns) break;
             __nanosleep(256);
         }
     }
@@ -94,8 +109,25 @@ __device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, int 
     return false;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
-    return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, err, code);
+// a pipeline wait: gives up early once any role has failed
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code,
+                                          unsigned long long limit_ns) {
+    return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, err, code, limit_ns, true);
+}
+
+// a wait for asynchronous work this kernel issued (MMAs, TMA copies) to settle before the
+// CTA leaves: bounded in time only, whatever the other roles did
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity, int *err, int code,
+                                           unsigned long long limit_ns) {
+    return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, err, code, limit_ns, false);
+}
+
+__device__ __forceinline__ void mbar_complete_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
 }
 
 // Shared-memory matrix descriptor: K-major tile of 128 rows x 128 bytes written by TMA with
@@ -288,6 +320,7 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
     uint64_t *b_full = bars + 3, *b_empty = b_full + S;
     uint64_t *d_full = b_empty + S, *d_empty = d_full + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d_empty + 2);
+    uint32_t *loads = tmem_slot + 1;  // (A tiles, B stage fills) each CTA issued; the leader's copy
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
     const bool leader = rank == 0;
@@ -324,20 +357,23 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
             int stage = 0;
             uint32_t phase = 0;
             int it = 0;
+            uint32_t na = 0, nf = 0;
             bool ok = true;
             for (int u = cluster; u < P.nunits && ok; u += nclusters, it++) {
                 const int4 U = P.units[u];
-                if (it > 0 && !(ok = mbar_wait(a_empty, (uint32_t)(it - 1) & 1u, P.err, 1))) break;
+                if (it > 0 && !(ok = mbar_wait(a_empty, (uint32_t)(it - 1) & 1u, P.err, 1, P.wait_ns))) break;
                 if (leader) mbar_expect_tx(a_full, (uint32_t)(2 * KB * TILE_BYTES));
                 for (int kb = 0; kb < KB; kb++)
                     tma_load_2d_pair(sA + (size_t)kb * TILE_BYTES, &tmap, a_full_l, kb * KBLK,
                                      U.x * PAIR_ROWS + (int)rank * TILE_ROWS);
+                na++;
                 for (int bc = U.y; bc < U.z && ok; bc++) {
                     for (int kb = 0; kb < KB; kb++) {
-                        if (!(ok = mbar_wait(&b_empty[stage], phase ^ 1u, P.err, 2))) break;
+                        if (!(ok = mbar_wait(&b_empty[stage], phase ^ 1u, P.err, 2, P.wait_ns))) break;
                         if (leader) mbar_expect_tx(&b_full[stage], (uint32_t)(2 * TILE_BYTES));
                         tma_load_2d_pair(sB + (size_t)stage * TILE_BYTES, &tmap, map_to_rank(&b_full[stage], 0),
                                          kb * KBLK, bc * PAIR_ROWS + (int)rank * TILE_ROWS);
+                        nf++;
                         if (++stage == S) {
                             stage = 0;
                             phase ^= 1u;
@@ -345,6 +381,9 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
                     }
                 }
             }
+            // the leader settles every copy either CTA issued before the pair leaves
+            st_cluster_u32(map_to_rank(&loads[2 * rank], 0), na);
+            st_cluster_u32(map_to_rank(&loads[2 * rank + 1], 0), nf);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer (even CTA)
@@ -359,13 +398,13 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
             bool ok = true;
             for (int u = cluster; u < P.nunits && ok; u += nclusters, it++) {
                 const int4 U = P.units[u];
-                if (!(ok = mbar_wait(a_full, (uint32_t)it & 1u, P.err, 3))) break;
+                if (!(ok = mbar_wait(a_full, (uint32_t)it & 1u, P.err, 3, P.wait_ns))) break;
                 for (int bc = U.y; bc < U.z && ok; bc++) {
-                    if (!(ok = mbar_wait(&d_empty[buf], (uses[buf] & 1u) ^ 1u, P.err, 4))) break;
+                    if (!(ok = mbar_wait(&d_empty[buf], (uses[buf] & 1u) ^ 1u ^ P.stall, P.err, 4, P.wait_ns))) break;
                     tc_fence_after();
                     const uint32_t td = tmem + (uint32_t)(buf * 256);
                     for (int kb = 0; kb < KB; kb++) {
-                        if (!(ok = mbar_wait(&b_full[stage], phase, P.err, 5))) break;
+                        if (!(ok = mbar_wait(&b_full[stage], phase, P.err, 5, P.wait_ns))) break;
                         const uint64_t bdesc = bdesc0 + (uint64_t)(stage * (TILE_BYTES >> 4));
                         const uint64_t adesc = adesc0 + (uint64_t)(kb * (TILE_BYTES >> 4));
 #pragma unroll
@@ -385,7 +424,7 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
                 umma_commit_pair(a_empty);
             }
             umma_commit_pair(done);
-            mbar_wait(done, 0, P.err, 6);
+            mbar_drain(done, 0, P.err, 6, P.wait_ns);  // every MMA has finished with TMEM and shared memory
         }
     } else {
         // ------------------------------------------------------------ epilogue (both CTAs)
@@ -399,7 +438,7 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
             const int4 U = P.units[u];
             const int i = U.x * PAIR_ROWS + (int)rank * TILE_ROWS + q * 32 + lane;
             for (int bc = U.y; bc < U.z; bc++) {
-                if (!(ok = __all_sync(0xffffffffu, mbar_wait(&d_full[buf], uses[buf] & 1u, P.err, 7)))) break;
+                if (!(ok = __all_sync(0xffffffffu, mbar_wait(&d_full[buf], uses[buf] & 1u, P.err, 7, P.wait_ns)))) break;
                 tc_fence_after();
                 uint32_t r[EPI_COLS];
                 const uint32_t col = (uint32_t)(buf * 256 + h * EPI_COLS);
@@ -423,7 +462,28 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
         slab_finish(w, P.cand, P.cap, P.padded);
     }
     __syncthreads();
-    cluster_sync_all();  // the peer no longer touches this CTA's barriers or tensor memory
+    cluster_sync_all();  // every role of both CTAs is done; both load counts are published
+    if (leader && warp == 0 && lane == 0) {
+        // A phase of a_full / b_full[s] is left open when one CTA issued its half of a copy
+        // and the other did not (a wait ran out between the two): the missing half is
+        // accounted for, then the last phase is awaited, so no copy lands after exit. Within
+        // one barrier the CTAs' counts differ by at most one fill, and every earlier phase
+        // has completed (the MMA waited on it before the refill was allowed).
+        const uint32_t naL = loads[0], nfL = loads[1], naO = loads[2], nfO = loads[3];
+        for (int b = -1; b < S; b++) {
+            uint64_t *bar = b < 0 ? a_full : &b_full[b];
+            const uint32_t half = b < 0 ? (uint32_t)(KB * TILE_BYTES) : (uint32_t)TILE_BYTES;
+            const uint32_t cL = b < 0 ? naL : nfL / S + ((uint32_t)b < nfL % S ? 1u : 0u);
+            const uint32_t cO = b < 0 ? naO : nfO / S + ((uint32_t)b < nfO % S ? 1u : 0u);
+            const uint32_t c = max(cL, cO);
+            if (c == 0) continue;
+            if (cL > cO) mbar_complete_tx(bar, half);  // armed for both halves; the peer's never left
+            if (cO > cL) mbar_expect_tx(bar, half);    // the peer's half was never armed for
+            mbar_drain(bar, (c - 1) & 1u, P.err, 8, P.wait_ns);
+        }
+    }
+    __syncwarp();
+    cluster_sync_all();  // the peer no longer touches this CTA's barriers, copies or tensor memory
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -578,8 +638,15 @@ aps_status encode_map(CUtensorMap *map, void *base, int64_t rows, int d) {
 }
 
 std::atomic<int64_t> g_dense_hint{0};
+std::atomic<int64_t> g_dense_stall{0};                // launches left to stall (test hook)
+std::atomic<unsigned long long> g_dense_stall_ns{0};  // their wait limit; 0 = the default
 
 }  // namespace
+
+void dense_debug_stall(int64_t launches, uint64_t wait_ns) {
+    g_dense_stall_ns.store(wait_ns);
+    g_dense_stall.store(launches > 0 ? launches : 0);
+}
 
 // Margin of the BF16 candidate test for unit vectors of dimension d: rounding both operands
 // to BF16 (unit roundoff 2^-8) changes x.y by at most (2u + u^2) ||x|| ||y||, the float32
@@ -677,6 +744,14 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
         P.count = ctr.p;
         P.padded = ctr.p + 2;
         P.err = err.p;
+        P.wait_ns = WAIT_NS_DEFAULT;
+        P.stall = 0;
+        for (int64_t k = g_dense_stall.load(); k > 0;)
+            if (g_dense_stall.compare_exchange_weak(k, k - 1)) {
+                P.stall = 1;
+                if (g_dense_stall_ns.load()) P.wait_ns = g_dense_stall_ns.load();
+                break;
+            }
         cudaLaunchConfig_t cfg;
         memset(&cfg, 0, sizeof(cfg));
         cfg.gridDim = dim3((unsigned)(2 * npairs_sm));

@@ -156,6 +156,7 @@ aps_status dense_all_pairs(const float *X, int32_t n, int32_t d, float t, uint32
 aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t, cudaStream_t s, aps_pairs *out,
                                   aps_stats *stats);
 double dense_margin(int d);
+void dense_debug_stall(int64_t launches, uint64_t wait_ns);
 
 // The similarity graph G_S as a CSR adjacency from a pair list, its k nearest neighbours,
 // and its release (graph.cu).

@@ -140,3 +140,34 @@ def test_dense_misaligned_device_rows(aps):
         aps.aps_pairs_free(p)
     compare(i, j, s, oracle.dense_all_pairs(X, f32(t)), f32(t), 1000)
 
+
+
+@pytest.mark.parametrize("n,d,wait_ns", [(1024, 128, 50_000_000), (40_000, 256, 0)])
+def test_dense_wait_limit_expires_and_context_stays_usable(aps, n, d, wait_ns):
+    """The tensor-core kernel's bounded waits: with the MMA issuer held back (a release
+    that never comes) every pipeline wait runs out, the kernel settles its copies, frees
+    tensor memory and returns; the call reports APS_ETIMEOUT within seconds and the next
+    join on the same context is exact. At 40k x 256 the TMA ring is full when the waits
+    expire; wait_ns = 0 takes the default limit."""
+    import time
+
+    import paper_1402_3010_gb300 as A
+
+    X = synth.dense_mixture(n, d, max(30, n // 100), 0.15, seed=n)
+    t = 0.8
+    before = run_dense(aps, X, t)
+    A.aps_debug_dense_stall(1, wait_ns)
+    t0 = time.time()
+    try:
+        with pytest.raises(A.APSError) as e:
+            run_dense(aps, X, t)
+    finally:
+        A.aps_debug_dense_stall(0)
+    assert e.value.status == A.ETIMEOUT
+    assert time.time() - t0 < 20
+    after = run_dense(aps, X, t)
+    for a, b in zip(before[:3], after[:3]):
+        assert np.array_equal(a, b)
+    if n <= 2000:
+        ref = oracle.dense_all_pairs(X, f32(t))
+        assert compare(after[0], after[1], after[2], ref, f32(t), n)["pairs"] > 0
