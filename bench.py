@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=600, help="queries per core in the oracle's timed sample")
     ap.add_argument("--cpu-cores", type=int, default=0, help="host cores for the CPU baseline (0: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched workload: time the default tile table instead of the autotuned one")
     ap.add_argument("--workload", default="sparse", choices=["sparse", "dense", "batched", "serving", "ablation", "graph", "horizontal", "vertical"],
                     help="sparse: the 200k-vector sparse self-join (default line); dense: the 200k x 256 "
                          "embedding self-join on the tensor cores; batched: 512 independent sparse "
@@ -551,6 +553,17 @@ def run_batched(args):
             aps.aps_pairs_free(o)
         return st, cnt
 
+    # tile shapes per size bucket, chosen by the autotuner on this batch (untimed setup)
+    tuned = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        groups, rep = aps.aps_autotune_batch_csr(ro, ip, ix, vv, m, t, 0, stream)
+        tuned = {"groups": groups, "default": aps.aps_tuning_default(),
+                 "bucket_bounds": [b for b in aps.TUNE_BOUNDS], "seconds": round(time.perf_counter() - t0, 2),
+                 "ms_join_default": round(rep["ms_default"], 3), "ms_join_tuned": round(rep["ms_tuned"], 3),
+                 "ms_per_group_count": {str(b): rep["ms"][b] for b in range(aps.TUNE_BUCKETS)
+                                        if rep["instances"][b] > 0},
+                 "instances": rep["instances"], "sampled": rep["sampled"]}
     for _ in range(max(args.warmup, 3)):
         flush.fill_(1.0)
         st, cnt = step()
@@ -583,6 +596,7 @@ def run_batched(args):
                       "call": st["ms_total"]},
         "work": {k: st[k] for k in ("visits", "candidates", "verified", "pairs", "band")},
         "gpu_launches": launches, "e2e": None, "clocks": clk,
+        "tiles": tuned if tuned is not None else {"groups": aps.aps_get_tuning(), "autotuned": False},
     }
     if not args.no_cpu_baseline:
         sel = np.random.default_rng(11).choice(len(ns), 24, replace=False)

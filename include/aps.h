@@ -205,7 +205,8 @@ typedef struct aps_instance {
 } aps_instance;
 
 /* Self-join of k independent instances in one pass: all instances are indexed by one
- * set of kernels and joined by one persistent launch per size class. outs[k] receives
+ * set of kernels and joined by one persistent launch (the size classes in turn, tile
+ * shapes from the table of aps_set_tuning / aps_autotune_batch_csr). outs[k] receives
  * instance k's pairs (i < j, local row ids, sorted); all k results share one allocation,
  * released by calling aps_pairs_free on every element. stats (may be NULL) gets the
  * totals. */
@@ -222,6 +223,52 @@ aps_status aps_batch_all_pairs_csr(int32_t k, const int64_t *row_offsets, const 
                                    const int32_t *idx, const float *val, const int32_t *m,
                                    const float *t, uint32_t flags, void *stream, aps_pairs *outs,
                                    aps_stats *stats);
+
+/* ---- join tile shapes and the autotuner ------------------------------------------ */
+/* The join's tile shape for an instance of n vectors: G query groups per CTA (1, 2, 4 or
+ * 8), each with a candidate window of 40960 / G ids in shared memory (the blocks of
+ * Sec. 5.1.9 as CTA-level tiles). G is looked up by the instance's size bucket: bucket b
+ * holds 1 + the previous bound <= n <= APS_TUNE_BOUND_b, with bounds 512, 1280, 2560,
+ * 5120, 10240, 20480, 40960 and unbounded (aps_tune_bucket). The bucket bounds are the
+ * work-split thresholds; the table is process-wide and read by every later index build
+ * (aps_build_index and the batched calls). */
+#define APS_TUNE_BUCKETS 8
+
+typedef struct aps_tuning {
+    int32_t groups[APS_TUNE_BUCKETS]; /* G per size bucket: 1, 2, 4 or 8 */
+} aps_tuning;
+
+typedef struct aps_tune_report {
+    int32_t instances[APS_TUNE_BUCKETS]; /* instances of the batch per bucket */
+    int32_t sampled[APS_TUNE_BUCKETS];   /* of those, in the timed sample */
+    float ms[APS_TUNE_BUCKETS][4];       /* sample join ms with G = 1, 2, 4, 8 (-1: not run) */
+    float ms_default;                    /* whole-batch join ms with the default table */
+    float ms_tuned;                      /* whole-batch join ms with the chosen table */
+    int32_t kept_default;                /* 1: the measured table was not faster overall */
+    int32_t _reserved;
+} aps_tune_report;
+
+/* The size bucket (0 .. APS_TUNE_BUCKETS-1) of an instance of n vectors. */
+int32_t aps_tune_bucket(int64_t n);
+/* The built-in table: G = 8 up to 5120 vectors (one window), 4 up to 10240, 2 above. */
+void aps_tuning_default(aps_tuning *out);
+/* The table in force for this process. */
+void aps_get_tuning(aps_tuning *out);
+/* Replace the table in force (APS_EINVAL unless every entry is 1, 2, 4 or 8). Affects
+ * index builds that start afterwards; built indexes keep their shapes. */
+aps_status aps_set_tuning(const aps_tuning *tuning);
+/* Autotuner for a batch given as in aps_batch_all_pairs_csr. For each size bucket the
+ * batch populates, a sample of its instances (whole instances, at most 2^18 vectors,
+ * spread over the bucket) is indexed with each G in {1, 2, 4, 8} and joined three times;
+ * the bucket takes the G with the least join time (the current entry unless another is
+ * at least 2% faster). The chosen table is then timed against the default on the whole
+ * batch (two joins each) and kept only if faster. The winner is installed
+ * (aps_set_tuning) and returned in *out; *report (may be NULL) gets the measurements.
+ * Results of the batch do not depend on the table; only the join time does. */
+aps_status aps_autotune_batch_csr(int32_t k, const int64_t *row_offsets, const int64_t *indptr,
+                                  const int32_t *idx, const float *val, const int32_t *m,
+                                  const float *t, uint32_t flags, void *stream, aps_tuning *out,
+                                  aps_tune_report *report);
 
 /* ---- dense embeddings ----------------------------------------------------------- */
 /* All pairs (i < j) of n unit vectors X[n, d] (float32, row-major) with X_i . X_j >= t:

@@ -17,7 +17,8 @@ __all__ = [
     "APSError", "load", "lib_path",
     "aps_build_index", "aps_all_pairs", "aps_query", "aps_index_export", "aps_index_info",
     "aps_index_stats", "aps_index_free", "aps_pairs_free", "aps_pairs_copy_to",
-    "aps_batch_all_pairs", "aps_batch_all_pairs_csr", "aps_all_pairs_dense", "aps_server_create", "aps_stream_submit",
+    "aps_batch_all_pairs", "aps_batch_all_pairs_csr", "aps_tune_bucket", "aps_tuning_default", "aps_get_tuning",
+    "aps_set_tuning", "aps_autotune_batch_csr", "aps_all_pairs_dense", "aps_server_create", "aps_stream_submit",
     "aps_stream_poll", "aps_stream_cancel", "aps_server_free", "aps_last_error", "aps_version",
     "aps_debug_fail_alloc", "aps_debug_dense_stall", "aps_launch_count", "aps_all_pairs_noalloc", "pairs_to_numpy", "pairs_to_torch",
     "DEVICE_PTRS", "NORMALIZE", "QUERYABLE", "NO_PARTIAL_INDEX", "NO_MINSIZE", "NO_REMSCORE",
@@ -67,6 +68,26 @@ class aps_pairs(ctypes.Structure):
 class aps_graph(ctypes.Structure):
     _fields_ = [("n", _i32), ("on_device", _i32), ("nnz", _i64), ("row_ptr", _P), ("col", _P), ("w", _P),
                 ("_priv", _P)]
+
+
+TUNE_BUCKETS = 8
+TUNE_BOUNDS = (512, 1280, 2560, 5120, 10240, 20480, 40960, None)  # None: unbounded
+
+
+class aps_tuning(ctypes.Structure):
+    _fields_ = [("groups", _i32 * TUNE_BUCKETS)]
+
+
+class aps_tune_report(ctypes.Structure):
+    _fields_ = [("instances", _i32 * TUNE_BUCKETS), ("sampled", _i32 * TUNE_BUCKETS),
+                ("ms", (_f32 * 4) * TUNE_BUCKETS), ("ms_default", _f32), ("ms_tuned", _f32),
+                ("kept_default", _i32), ("_reserved", _i32)]
+
+    def as_dict(self):
+        return {"instances": list(self.instances), "sampled": list(self.sampled),
+                "ms": [[round(float(v), 4) for v in row] for row in self.ms],
+                "ms_default": float(self.ms_default), "ms_tuned": float(self.ms_tuned),
+                "kept_default": int(self.kept_default)}
 
 
 class aps_stats(ctypes.Structure):
@@ -125,6 +146,12 @@ def load():
             "aps_pairs_copy_to": (_i32, [ctypes.POINTER(aps_pairs), _P, _P, _P, _P]),
             "aps_batch_all_pairs": (_i32, [_i32, ctypes.POINTER(aps_instance), _u32, _P,
                                            ctypes.POINTER(aps_pairs), ctypes.POINTER(aps_stats)]),
+            "aps_tune_bucket": (_i32, [_i64]),
+            "aps_tuning_default": (None, [ctypes.POINTER(aps_tuning)]),
+            "aps_get_tuning": (None, [ctypes.POINTER(aps_tuning)]),
+            "aps_set_tuning": (_i32, [ctypes.POINTER(aps_tuning)]),
+            "aps_autotune_batch_csr": (_i32, [_i32, _P, _P, _P, _P, _P, _P, _u32, _P, ctypes.POINTER(aps_tuning),
+                                              ctypes.POINTER(aps_tune_report)]),
             "aps_batch_all_pairs_csr": (_i32, [_i32, _P, _P, _P, _P, _P, _P, _u32, _P, ctypes.POINTER(aps_pairs),
                                                ctypes.POINTER(aps_stats)]),
             "aps_all_pairs_dense": (_i32, [_P, _i32, _i32, _f32, _u32, _P, ctypes.POINTER(aps_pairs),
@@ -368,6 +395,51 @@ def aps_batch_all_pairs_csr(row_offsets, indptr, idx, val, m, t, flags: int = 0,
     del keep
     _check(rc, "aps_batch_all_pairs_csr")
     return list(outs), st.as_dict()
+
+
+def aps_tune_bucket(n: int) -> int:
+    return int(load().aps_tune_bucket(int(n)))
+
+
+def aps_tuning_default() -> list:
+    tu = aps_tuning()
+    load().aps_tuning_default(ctypes.byref(tu))
+    return list(tu.groups)
+
+
+def aps_get_tuning() -> list:
+    tu = aps_tuning()
+    load().aps_get_tuning(ctypes.byref(tu))
+    return list(tu.groups)
+
+
+def aps_set_tuning(groups) -> None:
+    """groups: TUNE_BUCKETS query-group counts (1, 2, 4 or 8), one per size bucket."""
+    g = list(groups)
+    if len(g) != TUNE_BUCKETS:
+        raise ValueError(f"need {TUNE_BUCKETS} entries")
+    tu = aps_tuning()
+    for b, v in enumerate(g):
+        tu.groups[b] = int(v)
+    _check(load().aps_set_tuning(ctypes.byref(tu)), "aps_set_tuning")
+
+
+def aps_autotune_batch_csr(row_offsets, indptr, idx, val, m, t, flags: int = 0, stream=None):
+    """Time the join of each size bucket's sample under G = 1, 2, 4, 8 and install the
+    fastest table (arguments as aps_batch_all_pairs_csr). Returns (groups, report dict)."""
+    lib = load()
+    ro = np.ascontiguousarray(row_offsets, dtype=np.int64)
+    mm = np.ascontiguousarray(m, dtype=np.int32)
+    tt = np.ascontiguousarray(t, dtype=np.float32)
+    k = int(ro.size - 1)
+    (p0, p1, p2), f, keep = _csr_args(indptr, idx, val)
+    tu = aps_tuning()
+    rep = aps_tune_report()
+    rc = lib.aps_autotune_batch_csr(k, ro.ctypes.data, p0, p1, p2, mm.ctypes.data, tt.ctypes.data, int(flags) | f,
+                                    _stream_ptr(stream), ctypes.byref(tu), ctypes.byref(rep))
+    del keep
+    _check(rc, "aps_autotune_batch_csr")
+    return list(tu.groups), rep.as_dict()
 
 
 def aps_all_pairs_dense(X, t: float, flags: int = 0, stream=None):

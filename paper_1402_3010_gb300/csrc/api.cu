@@ -458,6 +458,63 @@ aps_status aps_batch_all_pairs_csr(int32_t k, const int64_t *row_offsets, const 
     return st;
 }
 
+int32_t aps_tune_bucket(int64_t n) { return tune_bucket(n); }
+
+void aps_tuning_default(aps_tuning *out) {
+    if (out) *out = tuning_default();
+}
+
+void aps_get_tuning(aps_tuning *out) {
+    if (out) *out = tuning_current();
+}
+
+aps_status aps_set_tuning(const aps_tuning *tuning) {
+    if (!tuning || !tuning_valid(*tuning)) {
+        set_error("a tuning table needs 1, 2, 4 or 8 query groups in every bucket");
+        return APS_EINVAL;
+    }
+    tuning_set(*tuning);
+    return APS_OK;
+}
+
+aps_status aps_autotune_batch_csr(int32_t k, const int64_t *row_offsets, const int64_t *indptr, const int32_t *idx,
+                                  const float *val, const int32_t *m, const float *t, uint32_t flags, void *stream,
+                                  aps_tuning *out, aps_tune_report *report) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (k < 1 || !row_offsets || !indptr || !m || !t || !out) {
+        set_error("need k >= 1 and non-NULL row_offsets, indptr, m, t, out");
+        return APS_EINVAL;
+    }
+    if (row_offsets[0] != 0) {
+        set_error("row_offsets[0] must be 0");
+        return APS_EINVAL;
+    }
+    for (int i = 0; i < k; i++) {
+        const int64_t n = row_offsets[i + 1] - row_offsets[i];
+        if (n < 0 || n >= (1ll << 31) || m[i] < 1) {
+            set_error("instance %d: need 0 <= n < 2^31 and m >= 1", i);
+            return APS_EINVAL;
+        }
+        APS_TRY(check_threshold(t[i]));
+    }
+    const int64_t N = row_offsets[k];
+    HostCsrCopy c;
+    const int64_t *dp;
+    const int32_t *di;
+    const float *dv;
+    APS_TRY(stage_csr(indptr, idx, val, N, flags, s, c, &dp, &di, &dv));
+    // the sample CSRs are cut on the host side of the row pointers
+    std::vector<int64_t> hptr;
+    const int64_t *hp = indptr;
+    if (flags & APS_DEVICE_PTRS) {
+        hptr.resize((size_t)N + 1);
+        APS_CUDA(cudaMemcpyAsync(hptr.data(), indptr, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, s));
+        APS_CUDA(cudaStreamSynchronize(s));
+        hp = hptr.data();
+    }
+    return autotune_batch(k, row_offsets, hp, dp, di, dv, m, t, flags & ~(uint32_t)APS_HOST_OUTPUT, s, out, report);
+}
+
 aps_status aps_all_pairs_dense(const float *X, int32_t n, int32_t d, float t, uint32_t flags, void *stream,
                                aps_pairs *out, aps_stats *stats) {
     if (!out) {

@@ -341,7 +341,7 @@ const char *code_name(int c) {
 }  // namespace
 
 aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_t *idx, const float *val,
-                              const std::vector<InstDesc> &inst_in, cudaStream_t s) {
+                              const std::vector<InstDesc> &inst_in, cudaStream_t s, const aps_tuning *tune) {
     const int k = (int)inst_in.size();
     ix->k = k;
     ix->stream = s;
@@ -349,27 +349,14 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     std::vector<InstDesc> inst = inst_in;
     int64_t N = 0, M = 0, nqw = 0, nwptr = 0;
     int32_t maxm = 1, maxn = 1, maxnw = 1;
-    // Tuning knob: APS_JOIN_MIN_GROUPS = 1, 2, 4 or 8 query groups per CTA at least
-    // (smaller candidate windows, more queries in flight per SM).
-    // Measured on the 200k-vector workload (join ms): 1 group 71.7, 2 groups 65.0, 4 groups
-    // 65.6, 8 groups 72.9.
-    int gmin = 2;
-    if (const char *e = getenv("APS_JOIN_MIN_GROUPS")) {
-        int v = atoi(e);
-        gmin = v >= 8 ? 8 : v >= 4 ? 4 : v >= 2 ? 2 : 1;
-    }
+    // tile shape per instance: G query groups per CTA from the size-bucket table
+    const aps_tuning tu = tune ? *tune : tuning_current();
     for (int i = 0; i < k; i++) {
         InstDesc &I = inst[i];
         I.vbase = N;
         I.rbase = (int32_t)M;
-        if (I.n <= JOIN_WMAX / 8) { I.G = 8; I.W = JOIN_WMAX / 8; }
-        else if (I.n <= JOIN_WMAX / 4) { I.G = 4; I.W = JOIN_WMAX / 4; }
-        else if (I.n <= JOIN_WMAX / 2) { I.G = 2; I.W = JOIN_WMAX / 2; }
-        else { I.G = 1; I.W = JOIN_WMAX; }
-        if (I.G < gmin) {
-            I.G = gmin;
-            I.W = JOIN_WMAX / gmin;
-        }
+        I.G = tu.groups[tune_bucket(I.n)];
+        I.W = JOIN_WMAX / I.G;
         I.nw = I.n > 0 ? (int32_t)((I.n + I.W - 1) / I.W) : 0;
         I.packed = I.n < (1 << 24) ? 1 : 0;
         I.qwbase = nqw;

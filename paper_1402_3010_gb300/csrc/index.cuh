@@ -74,6 +74,23 @@ struct IndexArrays {
     DBuf<int2> post;
 };
 
+// The join phase of an index as a CUDA graph: the two workspace resets and the persistent
+// join launch, captured on the index's first join; later joins update the nodes' pointers
+// and launch parameters in the instantiated graph and replay it.
+struct JoinGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t reset_ctr = nullptr, reset_cnt = nullptr, join = nullptr;
+    int64_t launches = 0;
+    JoinGraph() = default;
+    JoinGraph(const JoinGraph &) = delete;
+    JoinGraph &operator=(const JoinGraph &) = delete;
+    ~JoinGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
 }  // namespace aps
 
 struct aps_index {
@@ -96,6 +113,7 @@ struct aps_index {
     int64_t class_begin[5] = {0, 0, 0, 0, 0};  // classes G = 1, 2, 4, 8
     // output sizing from the previous join
     int64_t hint_pairs = 0;
+    aps::JoinGraph jgraph;  // the join phase, replayed by every join of this index
     aps_stats stats{};
     std::mutex stats_mu;  // queries may run concurrently (serving slots)
 };
@@ -136,7 +154,18 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
 // val) with global row pointers (indptr[0] = 0). Inputs are device pointers.
 aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_t *idx,
                               const float *val, const std::vector<InstDesc> &inst_in,
-                              cudaStream_t s);
+                              cudaStream_t s, const aps_tuning *tune = nullptr);
+
+// Join tile shapes (tune.cu): the size bucket of an instance, the process-wide table of
+// query groups per bucket, and the autotuner (host arrays ro, hptr, m, t; device CSR).
+int tune_bucket(int64_t n);
+aps_tuning tuning_default();
+aps_tuning tuning_current();
+bool tuning_valid(const aps_tuning &tu);
+void tuning_set(const aps_tuning &tu);
+aps_status autotune_batch(int32_t k, const int64_t *ro, const int64_t *hptr, const int64_t *dp, const int32_t *di,
+                          const float *dv, const int32_t *m, const float *t, uint32_t flags, cudaStream_t s,
+                          aps_tuning *out, aps_tune_report *rep);
 
 // Self-join of every instance of the index; fills a device aps_pairs (i, j, score)
 // with per-instance ranges in pair_offsets_h (k+1 entries, may be null).

@@ -1,10 +1,10 @@
 // The inverted-index join (Alg. 2, Find-Matches, with the all-pairs-2 bounds) and the
 // output stage.
 //
-// One persistent kernel per size class. A CTA of 1024 threads runs G query groups
-// (G = 1, 2, 4, 8); each group owns a dense score array A over a window of W candidate
-// ids in shared memory (the paper's all-pairs-0-array accumulator, cut into windows
-// because n floats do not fit on chip). For a query x (a whole vector of the set, taken
+// One persistent launch takes every size class in turn. A CTA of 1024 threads runs G
+// query groups (G = 1, 2, 4, 8); each group owns a dense score array A over a window of W
+// candidate ids in shared memory (the paper's all-pairs-0-array accumulator, cut into
+// windows because n floats do not fit on chip). For a query x (a whole vector of the set, taken
 // from a cost-ordered work list) and each window of candidates y > x:
 //   1. accumulate: A[y] += x[i] * y[i] over the posting lists of x's components,
 //      first over the components with remscore >= t (these may create candidates, and
@@ -26,6 +26,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "index.cuh"
 
@@ -38,8 +39,11 @@ struct JoinParams {
     const InstDesc *inst;
     const int32_t *vinst;
     const int32_t *items;
-    int64_t item_begin, item_end;
-    int G;
+    // size classes, taken in order by one persistent launch: class c is the work-list range
+    // [cls_begin[c], cls_begin[c + 1]) run with cls_G[c] query groups per CTA
+    int ncls;
+    int cls_G[4];
+    int64_t cls_begin[5];
     const int2 *crow;    // rank-ordered rows {rank, value}
     const int4 *vmeta;   // {row offset, |x|, |x'|, maxweight(x')}
     const float *pnorm;  // ||y'||_2 upper bound
@@ -56,7 +60,7 @@ struct JoinParams {
     Segment *segs;                    // [slots]: the run of slot qw
     int32_t *cntq;
     unsigned long long *counters;  // visits, candidates, verified, pairs, band
-    unsigned long long *work;
+    unsigned long long *work;       // [ncls] work-list cursors
     int2 *scratch;                  // per-warp lists of emitted pairs, JOIN_ECAP each
     // query mode: items are external query rows matched against every indexed vector
     int qmode;
@@ -159,7 +163,17 @@ __device__ __forceinline__ float dot_prefix(const int2 *__restrict__ yr, int ys,
 
 __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int G = P.G;
+    const bool f_minsize = !(P.flags & APS_NO_MINSIZE);
+    const bool f_remscore = !(P.flags & APS_NO_REMSCORE);
+    const bool f_upper = !(P.flags & APS_NO_UPPERBOUND);
+    unsigned long long n_visits = 0, n_cand = 0, n_verified = 0, n_band = 0, n_pairs = 0;
+    // A CTA that finds a class's work list empty moves on to the next class and re-carves
+    // its shared memory for that class's G, so the classes share one launch and one tail.
+    for (int cls = 0; cls < P.ncls; cls++) {
+    const int64_t item_begin = P.cls_begin[cls], item_end = P.cls_begin[cls + 1];
+    if (item_end <= item_begin) continue;
+    const int G = P.cls_G[cls];
+    unsigned long long *const work = P.work + cls;
     const int GT = JOIN_THREADS / G;
     const int g = threadIdx.x / GT, gt = threadIdx.x % GT;
     const int lane = gt & 31, gw = gt >> 5, NW = GT >> 5;
@@ -179,21 +193,17 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     int64_t *bc = reinterpret_cast<int64_t *>(wcnt + 32);
     int2 *elist = P.scratch + ((size_t)blockIdx.x * NWARPS + (threadIdx.x >> 5)) * JOIN_ECAP;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const bool f_minsize = !(P.flags & APS_NO_MINSIZE);
-    const bool f_remscore = !(P.flags & APS_NO_REMSCORE);
-    const bool f_upper = !(P.flags & APS_NO_UPPERBOUND);
 
     for (int i = gt; i < WG; i += GT) A[i] = 0.f;
     for (int i = gt; i < WG / 32; i += GT) bm[i] = 0u;
     if (gt == 0) bc[3] = bc[4] = bc[5] = 0;  // this group's staging slab: base, used, size
-    unsigned long long n_visits = 0, n_cand = 0, n_verified = 0, n_band = 0, n_pairs = 0;
 
     for (;;) {
         gsync(G, g, GT);  // every thread is done with the previous item's broadcast slots
-        if (gt == 0) bc[0] = (int64_t)atomicAdd(P.work, 1ull) + P.item_begin;
+        if (gt == 0) bc[0] = (int64_t)atomicAdd(work, 1ull) + item_begin;
         gsync(G, g, GT);
         const int64_t it = bc[0];
-        if (it >= P.item_end) break;
+        if (it >= item_end) break;
         // x: a vector of the set (self-join: candidates are the later ids of its instance)
         // or an external query (all indexed vectors are candidates)
         const int64_t x = P.qmode ? it : (int64_t)P.items[it];
@@ -489,13 +499,15 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
             __syncwarp();
         }
     }
+    __syncthreads();  // every group is done with this class's layout of shared memory
+    }
     // flush counters (warp-reduce, one atomic per warp)
     unsigned long long v5[5] = {n_visits, n_cand, n_verified, n_pairs, n_band};
 #pragma unroll
     for (int k = 0; k < 5; k++) {
         unsigned long long v = v5[k];
         for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0 && v) atomicAdd(&P.counters[k], v);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&P.counters[k], v);
     }
 }
 
@@ -523,6 +535,92 @@ __global__ void k_inst_offsets(const InstDesc *__restrict__ inst, int k, const i
                                int64_t nqw, int64_t *out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= k; i += gridDim.x * blockDim.x)
         out[i] = i < k ? qwoff[inst[i].qwbase] : qwoff[nqw];
+}
+
+// The index's size classes as one launch's class list. Returns the CTA count (enough for
+// every class's groups, at most max_ctas) and sets *smem to the largest class layout used.
+int set_classes(JoinParams &P, const aps_index *ix, int max_ctas, int *smem) {
+    static const int Gs[4] = {1, 2, 4, 8};
+    P.ncls = 4;
+    int64_t groups = 0;
+    *smem = 0;
+    for (int c = 0; c < 4; c++) {
+        P.cls_G[c] = Gs[c];
+        P.cls_begin[c] = ix->class_begin[c];
+        const int64_t ni = ix->class_begin[c + 1] - ix->class_begin[c];
+        if (ni <= 0) continue;
+        groups += (ni + Gs[c] - 1) / Gs[c];
+        *smem = std::max(*smem, group_bytes(Gs[c]) * Gs[c]);
+    }
+    P.cls_begin[4] = ix->class_begin[4];
+    return (int)std::min<int64_t>(max_ctas, std::max<int64_t>(groups, 1));
+}
+
+// The join phase (reset the counters and the per-slot pair counts, then the persistent
+// join) as a CUDA graph: captured on the index's first join (on a private stream, so any
+// caller stream works, including the legacy default one), then replayed with the memset
+// targets and the kernel's parameters and grid updated in place for each later join.
+aps_status run_join_graph(aps_index *ix, JoinParams &P, int grid, int smem, unsigned long long *ctr, int32_t *cntq,
+                          cudaStream_t s) {
+    JoinGraph &G = ix->jgraph;
+    const size_t ctr_bytes = 16 * sizeof(unsigned long long), cnt_bytes = sizeof(int32_t) * (size_t)ix->nqw;
+    if (!G.exec) {
+        cudaStream_t cs = nullptr;
+        APS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemsetAsync(ctr, 0, ctr_bytes, cs);
+            cudaMemsetAsync(cntq, 0, cnt_bytes, cs);
+            join_kernel<<<grid, JOIN_THREADS, smem, cs>>>(P);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(cs, &g);
+            G.graph = g;
+        }
+        cudaStreamDestroy(cs);
+        APS_CUDA(e);
+        size_t nn = 0;
+        APS_CUDA(cudaGraphGetNodes(G.graph, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        APS_CUDA(cudaGraphGetNodes(G.graph, nodes.data(), &nn));
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType ty;
+            APS_CUDA(cudaGraphNodeGetType(nd, &ty));
+            if (ty == cudaGraphNodeTypeKernel) {
+                G.join = nd;
+            } else if (ty == cudaGraphNodeTypeMemset) {
+                cudaMemsetParams mp;
+                APS_CUDA(cudaGraphMemsetNodeGetParams(nd, &mp));
+                if (mp.dst == ctr) G.reset_ctr = nd;
+                if (mp.dst == cntq) G.reset_cnt = nd;
+            }
+        }
+        if (nn != 3 || !G.join || !G.reset_ctr || !G.reset_cnt) {
+            set_error("join graph: expected two memset nodes and one kernel node, captured %zu nodes", nn);
+            return APS_ECUDA;
+        }
+        APS_CUDA(cudaGraphInstantiate(&G.exec, G.graph, 0));
+    } else {
+        cudaMemsetParams mp;
+        APS_CUDA(cudaGraphMemsetNodeGetParams(G.reset_ctr, &mp));
+        mp.dst = ctr;
+        APS_CUDA(cudaGraphExecMemsetNodeSetParams(G.exec, G.reset_ctr, &mp));
+        APS_CUDA(cudaGraphMemsetNodeGetParams(G.reset_cnt, &mp));
+        mp.dst = cntq;
+        APS_CUDA(cudaGraphExecMemsetNodeSetParams(G.exec, G.reset_cnt, &mp));
+        void *args[1] = {&P};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        kp.func = reinterpret_cast<void *>(join_kernel);
+        kp.gridDim = dim3((unsigned)grid);
+        kp.blockDim = dim3(JOIN_THREADS);
+        kp.sharedMemBytes = (unsigned)smem;
+        kp.kernelParams = args;
+        APS_CUDA(cudaGraphExecKernelNodeSetParams(G.exec, G.join, &kp));
+    }
+    APS_CUDA(cudaGraphLaunch(G.exec, s));
+    count_launch();
+    G.launches++;
+    return APS_OK;
 }
 
 }  // namespace
@@ -563,19 +661,17 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     int reruns = 0;
     for (int attempt = 0; attempt < 3; attempt++) {
         APS_TRY(stage.alloc((size_t)stage_cap, s));
-        APS_CUDA(cudaMemsetAsync(ctr.p, 0, 16 * sizeof(unsigned long long), s));
-        if (ix->nqw) APS_CUDA(cudaMemsetAsync(cntq.p, 0, sizeof(int32_t) * ix->nqw, s));
-        APS_CUDA(cudaEventRecord(ev[0], s));
-        for (int c = 0; c < 4; c++) {
-            const int64_t b = ix->class_begin[c], e = ix->class_begin[c + 1];
-            if (e <= b) continue;
+        if (ix->class_begin[4] <= ix->class_begin[0]) {  // nothing to join: just the resets
+            APS_CUDA(cudaMemsetAsync(ctr.p, 0, 16 * sizeof(unsigned long long), s));
+            if (ix->nqw) APS_CUDA(cudaMemsetAsync(cntq.p, 0, sizeof(int32_t) * ix->nqw, s));
+            APS_CUDA(cudaEventRecord(ev[0], s));
+        } else {
             JoinParams P;
             P.inst = d.inst.p;
             P.vinst = d.vinst.p;
             P.items = ix->items.p;
-            P.item_begin = b;
-            P.item_end = e;
-            P.G = Gs[c];
+            int smem = 0;
+            const int grid = set_classes(P, ix, sms, &smem);
             P.crow = d.crow.p;
             P.vmeta = d.vmeta.p;
             P.pnorm = d.pnorm.p;
@@ -592,14 +688,11 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
             P.segs = segs.p;
             P.cntq = cntq.p;
             P.counters = ctr.p;
-            P.work = ctr.p + 8 + c;
+            P.work = ctr.p + 8;
             P.scratch = scratch.p;
             P.qmode = 0;
-            const int64_t nitems = e - b;
-            const int64_t groups_needed = (nitems + Gs[c] - 1) / Gs[c];
-            const int grid = (int)std::min<int64_t>(sms, std::max<int64_t>(groups_needed, 1));
-            join_kernel<<<grid, JOIN_THREADS, group_bytes(Gs[c]) * Gs[c], s>>>(P);
-            APS_LAUNCH_CHECK();
+            APS_CUDA(cudaEventRecord(ev[0], s));
+            APS_TRY(run_join_graph(ix, P, grid, smem, ctr.p, cntq.p, s));
         }
         APS_CUDA(cudaEventRecord(ev[1], s));
         APS_CUDA(cudaMemcpyAsync(ch, ctr.p, sizeof(ch), cudaMemcpyDeviceToHost, s));
@@ -804,16 +897,13 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
     APS_CUDA(cudaFuncSetAttribute(join_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
     APS_CUDA(cudaMemsetAsync(ctr, 0, 16 * sizeof(unsigned long long), s));
     APS_CUDA(cudaMemsetAsync(cntq, 0, sizeof(int32_t) * nqw, s));
-    for (int c = 0; c < 4; c++) {
-        const int64_t b = ix->class_begin[c], e = ix->class_begin[c + 1];
-        if (e <= b) continue;
+    if (ix->class_begin[4] > ix->class_begin[0]) {
         JoinParams P;
         P.inst = d.inst.p;
         P.vinst = d.vinst.p;
         P.items = ix->items.p;
-        P.item_begin = b;
-        P.item_end = e;
-        P.G = Gs[c];
+        int smem = 0;
+        const int grid = set_classes(P, ix, grid_max, &smem);
         P.crow = d.crow.p;
         P.vmeta = d.vmeta.p;
         P.pnorm = d.pnorm.p;
@@ -830,12 +920,10 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
         P.segs = segs;
         P.cntq = cntq;
         P.counters = ctr;
-        P.work = ctr + 8 + c;
+        P.work = ctr + 8;
         P.scratch = elists;
         P.qmode = 0;
-        const int64_t groups_needed = (e - b + Gs[c] - 1) / Gs[c];
-        const int grid = (int)std::min<int64_t>(grid_max, std::max<int64_t>(groups_needed, 1));
-        join_kernel<<<grid, JOIN_THREADS, group_bytes(Gs[c]) * Gs[c], s>>>(P);
+        join_kernel<<<grid, JOIN_THREADS, smem, s>>>(P);
         APS_LAUNCH_CHECK();
     }
     unsigned long long ch[16];
@@ -906,9 +994,10 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
             P.inst = d.inst.p;
             P.vinst = d.vinst.p;
             P.items = nullptr;
-            P.item_begin = 0;
-            P.item_end = nq;
-            P.G = G;
+            P.ncls = 1;
+            P.cls_G[0] = G;
+            P.cls_begin[0] = 0;
+            P.cls_begin[1] = nq;
             P.crow = d.crow.p;
             P.vmeta = d.vmeta.p;
             P.pnorm = d.pnorm.p;
