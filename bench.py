@@ -505,13 +505,44 @@ def run_dense(args, rank, world):
 
         rows = np.random.default_rng(7).choice(n, 2000, replace=False)
         t0 = time.perf_counter()
-        oracle.dense_rows(X, t, rows)
+        ref = oracle.dense_rows(X, t, rows)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": len(rows) * (n - 1) / dt, "unit": UNIT, "cores": os.cpu_count(),
                                 "kind": "oracle",
                                 "sample": f"float64 NumPy X[rows] @ X.T + threshold for 2000 random rows "
                                           f"({len(rows) * (n - 1)} evaluations) in {dt:.2f} s (BLAS threads)"}
+        # error against FP64 on the same rows, from one more (untimed) call of the path
+        p, _ = aps.aps_all_pairs_dense(Xd, t, 0, stream)
+        try:
+            gi, gj, gs = aps.pairs_to_numpy(p)
+        finally:
+            aps.aps_pairs_free(p)
+        line["precision_vs_fp64"] = dense_precision(X, t, rows, gi, gj, gs, ref)
     return line
+
+
+def dense_precision(X, t, rows, gi, gj, gs, ref, band=1e-5):
+    """The path's pairs touching `rows` against the float64 scores of the same rows: max and
+    mean |score - fp64| over the common pairs, and the pairs one side has and the other lacks,
+    split by whether their fp64 score lies within `band` of t (only those may differ)."""
+    n = X.shape[0]
+    sel = np.isin(gi, rows) | np.isin(gj, rows)
+    gk = gi[sel].astype(np.int64) * n + gj[sel]
+    g_s = gs[sel].astype(np.float64)
+    rk = ref.i.astype(np.int64) * n + ref.j
+    rmap = dict(zip(rk.tolist(), np.asarray(ref.s, np.float64).tolist()))
+    gmap = dict(zip(gk.tolist(), g_s.tolist()))
+    common = [k for k in gmap if k in rmap]
+    err = np.array([abs(gmap[k] - rmap[k]) for k in common]) if common else np.zeros(1)
+    missing = [rmap[k] for k in rmap if k not in gmap]
+    extra = [k for k in gmap if k not in rmap]
+    X64 = np.asarray(X, dtype=np.float64)
+    extra_fp64 = [float(X64[k // n] @ X64[k % n]) for k in extra]
+    m_out = sum(abs(v - t) > band for v in missing)
+    e_out = sum(abs(v - t) > band for v in extra_fp64)
+    return {"rows": int(len(rows)), "pairs_checked": len(common), "max_abs_err": float(err.max()),
+            "mean_abs_err": float(err.mean()), "missing_outside_band": m_out, "missing_in_band": len(missing) - m_out,
+            "extra_outside_band": e_out, "extra_in_band": len(extra) - e_out, "band": band}
 
 
 BATCHED_WORKLOAD = ("batched sparse all-pairs: 512 independent instances, n log-uniform in [100, 20000], m=50000, "
