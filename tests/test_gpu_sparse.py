@@ -416,34 +416,40 @@ def test_batched_concatenated_csr_matches_per_instance_oracle(aps):
             A.aps_pairs_free(o)
 
 
-def test_full_size_200k_sampled_rows(aps):
-    """The 200k x 100k power-law workload at t = 0.7 in the bench's configuration (device
-    CSR, default flags): 40 sampled vectors' pairs checked one by one against the oracle's
-    float64 brute force over the whole set, plus the global form of the result."""
+@pytest.mark.parametrize("t", [0.5, 0.7, 0.9])
+def test_full_size_200k_sampled_rows(aps, t):
+    """The 200k x 100k power-law workload at each threshold of its sweep, in the bench's
+    configuration (device CSR, default flags): 40 sampled vectors' pairs checked one by one
+    against the oracle's float64 brute force over the whole set, plus the global form of
+    the result (checked on the device, where the pairs stay)."""
     import torch
 
     c = synth.config_large()
-    t = f32(0.7)
+    t = f32(t)
     dev = [torch.from_numpy(a).cuda() for a in (c.indptr, c.idx, c.val)]
     h = aps.aps_build_index(*dev, c.n, c.m, t)
     try:
         p = aps.aps_all_pairs(h)
         try:
-            i, j, s = aps.pairs_to_numpy(p)
+            gi, gj, gs = aps.pairs_to_torch(p)
         finally:
             aps.aps_pairs_free(p)
         st = aps.aps_index_stats(h)
     finally:
         aps.aps_index_free(h)
-    keys = i.astype(np.int64) * c.n + j
-    assert len(i) == st["pairs"] > 10_000_000
-    assert np.all(np.diff(keys) > 0) and np.all(i < j)
+    assert gi.numel() == st["pairs"] > 1_000_000
+    gkeys = gi.long() * c.n + gj.long()
+    assert bool((gkeys[1:] > gkeys[:-1]).all()) and bool((gi < gj).all())
     rows = np.random.default_rng(3).choice(c.n, 40, replace=False)
+    rt = torch.from_numpy(rows.astype(np.int32)).cuda()
+    sel = torch.isin(gi, rt) | torch.isin(gj, rt)
+    keys = gkeys[sel].cpu().numpy()
+    s = gs[sel].cpu().numpy()
+    del gi, gj, gs, gkeys, sel
     ref = oracle.bruteforce_rows(c, t, rows)
-    sel = np.isin(i, rows) | np.isin(j, rows)
     rk = ref.keys(c.n)
     rmap = dict(zip(rk.tolist(), ref.s.tolist()))
-    gmap = dict(zip(keys[sel].tolist(), s[sel].tolist()))
+    gmap = dict(zip(keys.tolist(), s.tolist()))
     assert len(rmap) > 0
     for k in set(rmap) - set(gmap):  # only pairs inside the 1e-5 band may differ
         assert abs(rmap[k] - t) <= 1e-5
