@@ -139,7 +139,9 @@ aps_status aps_build_index(const int64_t *indptr, const int32_t *idx, const floa
 /* Self-join of the indexed set at the build threshold: every pair (i < j) with
  * dot >= t (Alg. 1-2 with the all-pairs-2 bounds), sorted by (i, j).
  * flags: APS_NO_MINSIZE / APS_NO_REMSCORE / APS_NO_UPPERBOUND ablations and
- * APS_HOST_OUTPUT. Result buffers are allocated by the library; free with aps_pairs_free. */
+ * APS_HOST_OUTPUT. Result buffers are allocated by the library; free with aps_pairs_free.
+ * The first call on an index captures its join phase as a CUDA graph that later calls
+ * replay; calls on one index must not overlap each other (aps_query may run meanwhile). */
 aps_status aps_all_pairs(aps_index *index, uint32_t flags, aps_pairs *out);
 
 /* Match nq external query vectors (CSR as in aps_build_index) against the index

@@ -213,6 +213,7 @@ aps_status aps_index_stats(const aps_index *ix, aps_stats *out) {
         set_error("index and out must not be NULL");
         return APS_EINVAL;
     }
+    std::lock_guard<std::mutex> lk(ix->stats_mu);
     *out = ix->stats;
     return APS_OK;
 }

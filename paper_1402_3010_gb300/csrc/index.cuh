@@ -115,7 +115,7 @@ struct aps_index {
     int64_t hint_pairs = 0;
     aps::JoinGraph jgraph;  // the join phase, replayed by every join of this index
     aps_stats stats{};
-    std::mutex stats_mu;  // queries may run concurrently (serving slots)
+    mutable std::mutex stats_mu;  // queries may run concurrently (serving slots)
 };
 
 namespace aps {

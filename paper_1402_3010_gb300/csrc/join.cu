@@ -748,6 +748,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     float ms_join = 0, ms_sort = 0;
     cudaEventElapsedTime(&ms_join, ev[0], ev[1]);
     cudaEventElapsedTime(&ms_sort, ev[3], ev[2]);
+    std::lock_guard<std::mutex> lk(ix->stats_mu);  // queries may report meanwhile
     aps_stats &S = ix->stats;
     S.visits = (int64_t)ch[0];
     S.candidates = (int64_t)ch[1];
