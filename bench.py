@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--impl", default="aps", choices=["aps", "reference"])
     ap.add_argument("--n", type=int, default=200_000)
     ap.add_argument("--m", type=int, default=100_000)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=600, help="queries per core in the oracle's timed sample")
     ap.add_argument("--cpu-cores", type=int, default=0, help="host cores for the CPU baseline (0: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -330,12 +330,17 @@ def run_aps(args, rank, world):
         e2e_step()
         barrier()
         t0 = time.perf_counter()
-        outs = [e2e_step() for _ in range(args.e2e_steps)]
+        outs, marks = [], []
+        for _ in range(args.e2e_steps):
+            outs.append(e2e_step())
+            marks.append(time.perf_counter())
         barrier()
         dt = time.perf_counter() - t0
+        steps_ms = [round(1e3 * (b - a), 2) for a, b in zip([t0] + marks[:-1], marks)]
         dt = max_over_ranks(dt * 1e3, dev, world) * 1e-3  # the slowest rank's end-to-end time
         e2e = {"value": world * evals * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": hbytes,
-               "d2h_bytes_per_step": int(max(outs)) * 12, "ms_per_step": 1000 * dt / args.e2e_steps}
+               "d2h_bytes_per_step": int(max(outs)) * 12, "ms_per_step": 1000 * dt / args.e2e_steps,
+               "steps_ms": steps_ms}
 
     if rank != 0:
         return None
