@@ -362,6 +362,12 @@ void aps_debug_fail_alloc(int64_t k);
  * fault is involved. */
 void aps_debug_dense_stall(int64_t launches, uint64_t wait_ns);
 
+/* Test hook for the self-join's output staging: the next aps_all_pairs (or batched join)
+ * starts with room for `pairs` staged pairs instead of its estimate (0 disables), so a
+ * small value makes it overflow, grow the buffer and run the join again (stats.reruns).
+ * Host-side only; the kernel never writes past the room it was given. */
+void aps_debug_stage_cap(int64_t pairs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,8 @@ __all__ = [
     "aps_batch_all_pairs", "aps_batch_all_pairs_csr", "aps_tune_bucket", "aps_tuning_default", "aps_get_tuning",
     "aps_set_tuning", "aps_autotune_batch_csr", "aps_all_pairs_dense", "aps_server_create", "aps_stream_submit",
     "aps_stream_poll", "aps_stream_cancel", "aps_server_free", "aps_last_error", "aps_version",
-    "aps_debug_fail_alloc", "aps_debug_dense_stall", "aps_launch_count", "aps_all_pairs_noalloc", "pairs_to_numpy", "pairs_to_torch",
+    "aps_debug_fail_alloc", "aps_debug_dense_stall", "aps_debug_stage_cap", "aps_launch_count",
+    "aps_all_pairs_noalloc", "pairs_to_numpy", "pairs_to_torch",
     "DEVICE_PTRS", "NORMALIZE", "QUERYABLE", "NO_PARTIAL_INDEX", "NO_MINSIZE", "NO_REMSCORE",
     "NO_UPPERBOUND", "HOST_OUTPUT",
 ]
@@ -165,6 +166,7 @@ def load():
             "aps_version": (ctypes.c_char_p, []),
             "aps_debug_fail_alloc": (None, [_i64]),
             "aps_debug_dense_stall": (None, [_i64, _u64]),
+            "aps_debug_stage_cap": (None, [_i64]),
             "aps_launch_count": (_i64, []),
             "aps_all_pairs_noalloc": (_i32, [_P, _P, _P, _P, _i64, ctypes.POINTER(_i64), _P]),
             "aps_graph_csr": (_i32, [_P, _P, _P, _i64, _i32, _u32, _P, ctypes.POINTER(aps_graph)]),
@@ -203,6 +205,10 @@ def aps_debug_fail_alloc(k: int) -> None:
 
 def aps_debug_dense_stall(launches: int, wait_ns: int = 0) -> None:
     load().aps_debug_dense_stall(int(launches), int(wait_ns))
+
+
+def aps_debug_stage_cap(pairs: int) -> None:
+    load().aps_debug_stage_cap(int(pairs))
 
 
 def _check(st: int, where: str):

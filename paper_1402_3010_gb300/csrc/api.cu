@@ -542,6 +542,8 @@ void aps_debug_fail_alloc(int64_t k) { set_alloc_fault(k); }
 
 void aps_debug_dense_stall(int64_t launches, uint64_t wait_ns) { dense_debug_stall(launches, wait_ns); }
 
+void aps_debug_stage_cap(int64_t pairs) { debug_stage_cap(pairs); }
+
 aps_status aps_graph_csr(const int32_t *i, const int32_t *j, const float *s, int64_t count, int32_t n,
                          uint32_t flags, void *stream, aps_graph *out) {
     if (!out) {

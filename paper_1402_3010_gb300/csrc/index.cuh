@@ -186,6 +186,7 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
                                   aps_stats *stats);
 double dense_margin(int d);
 void dense_debug_stall(int64_t launches, uint64_t wait_ns);
+void debug_stage_cap(int64_t pairs);
 
 // The similarity graph G_S as a CSR adjacency from a pair list, its k nearest neighbours,
 // and its release (graph.cu).

@@ -34,6 +34,7 @@ namespace aps {
 namespace {
 
 std::atomic<int64_t> g_stage_hint{0};
+std::atomic<int64_t> g_stage_cap_once{0};  // test hook: staging room of the next self-join
 
 struct JoinParams {
     const InstDesc *inst;
@@ -625,6 +626,8 @@ aps_status run_join_graph(aps_index *ix, JoinParams &P, int grid, int smem, unsi
 
 }  // namespace
 
+void debug_stage_cap(int64_t pairs) { g_stage_cap_once.store(pairs > 0 ? pairs : 0); }
+
 aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::vector<int64_t> *pair_offsets_h) {
     cudaStream_t s = ix->stream;
     IndexArrays &d = ix->d;
@@ -651,6 +654,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     // that still overflows is re-run with room for what it reserved plus one slab per
     // group. Segments are stored per (vector, window) slot, so their table never overflows.
     int64_t stage_cap = std::max<int64_t>({ix->hint_pairs, g_stage_hint.load(), (int64_t)1 << 20, ix->nnz});
+    if (const int64_t once = g_stage_cap_once.exchange(0); once > 0) stage_cap = once;
     DBuf<int2> stage;
     DBuf<Segment> segs;
     DBuf<int2> scratch;

@@ -136,3 +136,33 @@ def test_repeated_joins_of_one_index_replay_the_join_graph(A):
         assert len(runs[0][0]) > 100
     finally:
         A.aps_index_free(h)
+
+
+def test_staging_overflow_grows_and_reruns_the_join(A):
+    """A join whose staging room is far too small (test hook: room for 1000 pairs) sees
+    its slab reservations exceed the room, grows the buffer and runs again: one re-run,
+    the oracle's pairs. The re-run replays the join graph with the new buffer."""
+    import torch
+
+    rng = np.random.default_rng(85)
+    lengths = synth.power_law_lengths(rng, 4000, synth.ALPHA_MEAN50, 1, 300)
+    c = synth.sparse_vectors(4000, 3000, lengths, 1.0, "lognormal", 85, rng=rng)
+    t = float(np.float32(0.6))
+    ip, ix, vv = (torch.from_numpy(a).cuda() for a in (c.indptr, c.idx, c.val))
+    ref = oracle.bruteforce(c, t)
+    assert len(ref.i) > 20_000
+    h = A.aps_build_index(ip, ix, vv, c.n, c.m, t, 0)
+    try:
+        for cap in (1000, 0):  # an overflowing join, then one with the estimate from it
+            A.aps_debug_stage_cap(cap)
+            p = A.aps_all_pairs(h)
+            try:
+                i, j, s = A.pairs_to_numpy(p)
+            finally:
+                A.aps_pairs_free(p)
+            st = A.aps_index_stats(h)
+            assert st["reruns"] == (1 if cap else 0)
+            compare(i, j, s, ref, t, c.n, csr=c)
+    finally:
+        A.aps_debug_stage_cap(0)
+        A.aps_index_free(h)
