@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=600, help="queries per core in the oracle's timed sample")
     ap.add_argument("--cpu-cores", type=int, default=0, help="host cores for the CPU baseline (0: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tiles", default="",
+                    help="query groups per size bucket (8 comma-separated values of 1, 2, 4, 8) installed "
+                         "before any index is built; default: the library's table")
+    ap.add_argument("--query-tiles", default="",
+                    help="the same for indexes built to answer queries (the serving index); default: the library's")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched workload: time the default tile table instead of the autotuned one")
     ap.add_argument("--workload", default="sparse", choices=["sparse", "dense", "batched", "serving", "ablation", "graph", "horizontal", "vertical"],
@@ -726,7 +731,7 @@ def run_serving(args):
         "dtype": "f32", "data": "synthetic (seeded generator, no dataset)",
         "config": {"workload": SERVING_WORKLOAD, "index_n": c.n, "index_nnz": c.nnz, "batches": len(batches),
                    "queries": int(offs[-1]), "slots": args.slots, "t": t, "parallelism": "single GPU",
-                   "pairs": pairs},
+                   "pairs": pairs, "tiles": aps.aps_get_tuning(query=True)},
         "serving": {"saturated_queries_per_s": qps,
                     "saturated_p50_ms": 1000 * float(np.percentile(lsat, 50)),
                     "saturated_p99_ms": 1000 * float(np.percentile(lsat, 99)), "poisson_load": loads},
@@ -1095,6 +1100,12 @@ def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if (args.tiles or args.query_tiles) and args.impl != "reference":
+        import paper_1402_3010_gb300 as aps
+
+        aps.load()
+        cols = [[int(v) for v in a.split(",")] if a else None for a in (args.tiles, args.query_tiles)]
+        aps.aps_set_tuning(cols[0] or aps.aps_get_tuning(), cols[1])
     if args.impl == "reference":
         line = run_reference(args, rank)
     elif args.workload == "dense":

@@ -237,7 +237,8 @@ aps_status aps_batch_all_pairs_csr(int32_t k, const int64_t *row_offsets, const 
 #define APS_TUNE_BUCKETS 8
 
 typedef struct aps_tuning {
-    int32_t groups[APS_TUNE_BUCKETS]; /* G per size bucket: 1, 2, 4 or 8 */
+    int32_t groups[APS_TUNE_BUCKETS];       /* G per size bucket: 1, 2, 4 or 8 */
+    int32_t query_groups[APS_TUNE_BUCKETS]; /* G for indexes built with APS_QUERYABLE */
 } aps_tuning;
 
 typedef struct aps_tune_report {
@@ -252,20 +253,24 @@ typedef struct aps_tune_report {
 
 /* The size bucket (0 .. APS_TUNE_BUCKETS-1) of an instance of n vectors. */
 int32_t aps_tune_bucket(int64_t n);
-/* The built-in table: G = 8 up to 5120 vectors (one window), 4 up to 10240, 2 above. */
+/* The built-in table. Self-joins: G = 8 up to 5120 vectors (one window), 4 up to 10240,
+ * 2 above. Queryable indexes, whose queries visit every window: the largest G that keeps
+ * the fewest windows (G = 1 above 20480 vectors). */
 void aps_tuning_default(aps_tuning *out);
 /* The table in force for this process. */
 void aps_get_tuning(aps_tuning *out);
-/* Replace the table in force (APS_EINVAL unless every entry is 1, 2, 4 or 8). Affects
- * index builds that start afterwards; built indexes keep their shapes. */
+/* Replace the table in force (APS_EINVAL unless every entry of both columns is 1, 2, 4
+ * or 8). Affects index builds that start afterwards; built indexes keep their shapes. */
 aps_status aps_set_tuning(const aps_tuning *tuning);
 /* Autotuner for a batch given as in aps_batch_all_pairs_csr. For each size bucket the
  * batch populates, a sample of its instances (whole instances, at most 2^18 vectors,
  * spread over the bucket) is indexed with each G in {1, 2, 4, 8} and joined three times;
  * the bucket takes the G with the least join time (the current entry unless another is
  * at least 2% faster). The chosen table is then timed against the default on the whole
- * batch (two joins each) and kept only if faster. The winner is installed
+ * batch (two joins each) and kept only if faster; the queryable column is left as it
+ * is. The winner is installed
  * (aps_set_tuning) and returned in *out; *report (may be NULL) gets the measurements.
+ * APS_QUERYABLE and APS_HOST_OUTPUT in flags are ignored (the self-join column is tuned).
  * Results of the batch do not depend on the table; only the join time does. */
 aps_status aps_autotune_batch_csr(int32_t k, const int64_t *row_offsets, const int64_t *indptr,
                                   const int32_t *idx, const float *val, const int32_t *m,

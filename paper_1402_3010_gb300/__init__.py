@@ -76,7 +76,7 @@ TUNE_BOUNDS = (512, 1280, 2560, 5120, 10240, 20480, 40960, None)  # None: unboun
 
 
 class aps_tuning(ctypes.Structure):
-    _fields_ = [("groups", _i32 * TUNE_BUCKETS)]
+    _fields_ = [("groups", _i32 * TUNE_BUCKETS), ("query_groups", _i32 * TUNE_BUCKETS)]
 
 
 class aps_tune_report(ctypes.Structure):
@@ -407,26 +407,34 @@ def aps_tune_bucket(n: int) -> int:
     return int(load().aps_tune_bucket(int(n)))
 
 
-def aps_tuning_default() -> list:
+def aps_tuning_default(query: bool = False) -> list:
+    """The built-in table's self-join column (query=True: its queryable-index column)."""
     tu = aps_tuning()
     load().aps_tuning_default(ctypes.byref(tu))
-    return list(tu.groups)
+    return list(tu.query_groups if query else tu.groups)
 
 
-def aps_get_tuning() -> list:
+def aps_get_tuning(query: bool = False) -> list:
+    """The table in force: its self-join column (query=True: its queryable-index column)."""
     tu = aps_tuning()
     load().aps_get_tuning(ctypes.byref(tu))
-    return list(tu.groups)
+    return list(tu.query_groups if query else tu.groups)
 
 
-def aps_set_tuning(groups) -> None:
-    """groups: TUNE_BUCKETS query-group counts (1, 2, 4 or 8), one per size bucket."""
-    g = list(groups)
-    if len(g) != TUNE_BUCKETS:
-        raise ValueError(f"need {TUNE_BUCKETS} entries")
+def aps_set_tuning(groups, query_groups=None) -> None:
+    """groups: TUNE_BUCKETS query-group counts (1, 2, 4 or 8), one per size bucket, for
+    self-joins; query_groups: the same for indexes built with QUERYABLE (None: unchanged)."""
+    cur = aps_tuning()
+    load().aps_get_tuning(ctypes.byref(cur))
+    cols = {"groups": groups, "query_groups": query_groups if query_groups is not None else list(cur.query_groups)}
     tu = aps_tuning()
-    for b, v in enumerate(g):
-        tu.groups[b] = int(v)
+    for name, vals in cols.items():
+        v = list(vals)
+        if len(v) != TUNE_BUCKETS:
+            raise ValueError(f"need {TUNE_BUCKETS} entries")
+        arr = getattr(tu, name)
+        for b, x in enumerate(v):
+            arr[b] = int(x)
     _check(load().aps_set_tuning(ctypes.byref(tu)), "aps_set_tuning")
 
 

@@ -513,7 +513,10 @@ aps_status aps_autotune_batch_csr(int32_t k, const int64_t *row_offsets, const i
         APS_CUDA(cudaStreamSynchronize(s));
         hp = hptr.data();
     }
-    return autotune_batch(k, row_offsets, hp, dp, di, dv, m, t, flags & ~(uint32_t)APS_HOST_OUTPUT, s, out, report);
+    // the self-join column is tuned: the timed joins take neither host output nor the
+    // queryable split
+    return autotune_batch(k, row_offsets, hp, dp, di, dv, m, t, flags & ~(uint32_t)(APS_HOST_OUTPUT | APS_QUERYABLE), s,
+                          out, report);
 }
 
 aps_status aps_all_pairs_dense(const float *X, int32_t n, int32_t d, float t, uint32_t flags, void *stream,

@@ -349,13 +349,15 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     std::vector<InstDesc> inst = inst_in;
     int64_t N = 0, M = 0, nqw = 0, nwptr = 0;
     int32_t maxm = 1, maxn = 1, maxnw = 1;
-    // tile shape per instance: G query groups per CTA from the size-bucket table
+    // tile shape per instance: G query groups per CTA from the size-bucket table (its
+    // queryable column for indexes built to answer queries)
     const aps_tuning tu = tune ? *tune : tuning_current();
+    const int32_t *gtab = (ix->flags & APS_QUERYABLE) ? tu.query_groups : tu.groups;
     for (int i = 0; i < k; i++) {
         InstDesc &I = inst[i];
         I.vbase = N;
         I.rbase = (int32_t)M;
-        I.G = tu.groups[tune_bucket(I.n)];
+        I.G = gtab[tune_bucket(I.n)];
         I.W = JOIN_WMAX / I.G;
         I.nw = I.n > 0 ? (int32_t)((I.n + I.W - 1) / I.W) : 0;
         I.packed = I.n < (1 << 24) ? 1 : 0;

@@ -21,10 +21,13 @@ namespace {
 const int64_t BOUNDS[APS_TUNE_BUCKETS] = {512, 1280, 2560, 5120, 10240, 20480, 40960, INT64_MAX};
 const int GS[4] = {1, 2, 4, 8};
 
-// Default: the largest G whose window still holds the whole instance (one window per
-// query), but at least 2 groups. Measured on the 200k-vector power-law set (join ms):
-// G = 1: 71.7, 2: 65.0, 4: 65.6, 8: 72.9.
-const aps_tuning DEFAULT_TUNING = {{8, 8, 8, 8, 4, 2, 2, 2}};
+// Default for self-joins: the largest G whose window still holds the whole instance (one
+// window per query), but at least 2 groups. Measured on the 200k-vector power-law set
+// (join ms): G = 1: 71.7, 2: 65.0, 4: 65.6, 8: 72.9.
+// Default for queryable indexes: a query visits every window of the index, so the fixed
+// cost per window dominates; the largest G that keeps the fewest windows. Measured on the
+// 1M-vector serving index (saturated queries/s): G = 1: 47,014, 2: 23,481, 4: 11,650.
+const aps_tuning DEFAULT_TUNING = {{8, 8, 8, 8, 4, 2, 2, 2}, {8, 8, 8, 8, 4, 2, 1, 1}};
 
 std::mutex g_tune_mu;
 aps_tuning g_tune = DEFAULT_TUNING;
@@ -114,10 +117,9 @@ aps_tuning tuning_current() {
 }
 
 bool tuning_valid(const aps_tuning &tu) {
-    for (int b = 0; b < APS_TUNE_BUCKETS; b++) {
-        const int g = tu.groups[b];
-        if (g != 1 && g != 2 && g != 4 && g != 8) return false;
-    }
+    for (int b = 0; b < APS_TUNE_BUCKETS; b++)
+        for (const int g : {tu.groups[b], tu.query_groups[b]})
+            if (g != 1 && g != 2 && g != 4 && g != 8) return false;
     return true;
 }
 
@@ -162,7 +164,7 @@ aps_status autotune_batch(int32_t k, const int64_t *ro, const int64_t *hptr, con
         float best = -1.f;
         int best_g = cur.groups[b];
         for (int gi = 0; gi < 4; gi++) {
-            aps_tuning force;
+            aps_tuning force = cur;
             for (int c = 0; c < APS_TUNE_BUCKETS; c++) force.groups[c] = GS[gi];
             float ms = -1.f;
             APS_TRY(time_join(sel, k, ro, hptr, dp, di, dv, m, t, flags, force, 3, s, &ms));
@@ -178,7 +180,8 @@ aps_status autotune_batch(int32_t k, const int64_t *ro, const int64_t *hptr, con
     // the whole batch: the chosen table against the default
     std::vector<int> all((size_t)k);
     for (int r = 0; r < k; r++) all[(size_t)r] = r;
-    const aps_tuning def = DEFAULT_TUNING;
+    aps_tuning def = DEFAULT_TUNING;
+    memcpy(def.query_groups, cur.query_groups, sizeof(def.query_groups));  // the queryable column stays
     APS_TRY(time_join(all, k, ro, hptr, dp, di, dv, m, t, flags, def, 2, s, &R.ms_default));
     if (memcmp(&tuned, &def, sizeof(def)) == 0) {
         R.ms_tuned = R.ms_default;

@@ -166,3 +166,36 @@ def test_staging_overflow_grows_and_reruns_the_join(A):
     finally:
         A.aps_debug_stage_cap(0)
         A.aps_index_free(h)
+
+
+def test_every_query_tile_shape_matches_the_oracle(A):
+    """A queryable index of 30000 vectors (three windows at G = 2, one at G = 1, six at
+    G = 8) built under each G of the queryable column, queried with 300 rows of the same
+    power-law family: the oracle's cross pairs every time."""
+    m = 12000
+    perm = np.random.default_rng(2087).permutation(m)
+    r1 = np.random.default_rng(87)
+    c = synth.sparse_vectors(30000, m, synth.power_law_lengths(r1, 30000, synth.ALPHA_MEAN40, 1, 300), 1.0,
+                             "lognormal", 87, rng=r1, perm=perm)
+    r2 = np.random.default_rng(88)
+    q = synth.sparse_vectors(300, m, synth.power_law_lengths(r2, 300, synth.ALPHA_MEAN40, 1, 300), 1.0,
+                             "lognormal", 88, rng=r2, perm=perm)
+    t = float(np.float32(0.7))
+    ref = oracle.bruteforce_cross(q, c, t)
+    assert len(ref.i) > 100
+    default_q = A.aps_tuning_default(query=True)
+    try:
+        for g in (1, 2, 4, 8):
+            A.aps_set_tuning(A.aps_tuning_default(), [g] * A.TUNE_BUCKETS)
+            h = A.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, t, A.QUERYABLE)
+            try:
+                p = A.aps_query(h, q.indptr, q.idx, q.val, q.n, t)
+                try:
+                    i, j, s = A.pairs_to_numpy(p)
+                finally:
+                    A.aps_pairs_free(p)
+            finally:
+                A.aps_index_free(h)
+            compare(i, j, s, ref, t, c.n, self_join=False)
+    finally:
+        A.aps_set_tuning(A.aps_tuning_default(), default_q)

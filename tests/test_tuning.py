@@ -9,7 +9,7 @@ def A():
 
     A.load()
     yield A
-    A.aps_set_tuning(A.aps_tuning_default())
+    A.aps_set_tuning(A.aps_tuning_default(), A.aps_tuning_default(query=True))
 
 
 def test_size_buckets_follow_their_bounds(A):
@@ -31,6 +31,16 @@ def test_default_table_is_the_one_window_rule(A):
         assert table[A.aps_tune_bucket(n)] == want, n
 
 
+def test_default_queryable_column_keeps_the_fewest_windows(A):
+    """Queryable indexes: the largest G in {1, 2, 4, 8} whose window count ceil(n / (40960 /
+    G)) equals that of G = 1 (a query visits every window)."""
+    table = A.aps_tuning_default(query=True)
+    for n in [1, 100, 512, 5120, 5121, 9000, 10240, 10241, 20480, 20481, 40960, 40961, 200000, 10**6]:
+        w1 = -(-n // 40960)
+        want = max(g for g in (1, 2, 4, 8) if -(-n // (40960 // g)) == w1)
+        assert table[A.aps_tune_bucket(n)] == want, n
+
+
 def test_set_and_get_round_trip_and_validation(A):
     A.aps_set_tuning([1, 2, 4, 8, 8, 4, 2, 1])
     assert A.aps_get_tuning() == [1, 2, 4, 8, 8, 4, 2, 1]
@@ -41,5 +51,8 @@ def test_set_and_get_round_trip_and_validation(A):
     assert A.aps_get_tuning() == [1, 2, 4, 8, 8, 4, 2, 1]  # a rejected table changes nothing
     with pytest.raises(ValueError):
         A.aps_set_tuning([8] * 7)
-    A.aps_set_tuning(A.aps_tuning_default())
+    with pytest.raises(A.APSError):
+        A.aps_set_tuning([8] * 8, [3] * 8)  # the queryable column is validated too
+    A.aps_set_tuning(A.aps_tuning_default(), A.aps_tuning_default(query=True))
     assert A.aps_get_tuning() == A.aps_tuning_default()
+    assert A.aps_get_tuning(query=True) == A.aps_tuning_default(query=True)
