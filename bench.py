@@ -322,6 +322,8 @@ def run_aps(args, rank, world):
         os_ = torch.empty(npairs, dtype=torch.float32).pin_memory()
         hbytes = c.indptr.nbytes + c.idx.nbytes + c.val.nbytes
 
+        gpu_ms = []
+
         def e2e_step():
             h = aps.aps_build_index(hip.numpy(), hix.numpy(), hvv.numpy(), c.n, c.m, t, 0, stream)
             p = aps.aps_all_pairs(h)
@@ -329,6 +331,8 @@ def run_aps(args, rank, world):
             if n_out <= npairs:
                 aps.aps_pairs_copy_to(p, oi.numpy(), oj.numpy(), os_.numpy(), stream)
             aps.aps_pairs_free(p)
+            s_ = aps.aps_index_stats(h)
+            gpu_ms.append([round(s_["ms_build"], 2), round(s_["ms_join"], 2), int(s_["reruns"])])
             aps.aps_index_free(h)
             return n_out
 
@@ -345,7 +349,8 @@ def run_aps(args, rank, world):
         dt = max_over_ranks(dt * 1e3, dev, world) * 1e-3  # the slowest rank's end-to-end time
         e2e = {"value": world * evals * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": hbytes,
                "d2h_bytes_per_step": int(max(outs)) * 12, "ms_per_step": 1000 * dt / args.e2e_steps,
-               "steps_ms": steps_ms}
+               "steps_ms": steps_ms,
+               "steps_library_ms": {"fields": ["build", "join (last attempt)", "reruns"], "steps": gpu_ms[1:]}}
 
     if rank != 0:
         return None

@@ -70,6 +70,7 @@ struct JoinParams {
     const int32_t *qqsplit;
     const float *qmw;
     float qt;
+    int qnw;              // windows of the index: query-mode items are (query, window) pairs
 };
 
 constexpr int NWARPS = JOIN_THREADS / 32;
@@ -162,6 +163,9 @@ __device__ __forceinline__ float dot_prefix(const int2 *__restrict__ yr, int ys,
     return acc;
 }
 
+// QMODE: external queries against the index (P.qmode = 1); compiled separately so that
+// the self-join carries none of the query path's state.
+template <bool QMODE>
 __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const bool f_minsize = !(P.flags & APS_NO_MINSIZE);
@@ -207,15 +211,18 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
         if (it >= item_end) break;
         // x: a vector of the set (self-join: candidates are the later ids of its instance)
         // or an external query (all indexed vectors are candidates)
-        const int64_t x = P.qmode ? it : (int64_t)P.items[it];
-        const InstDesc I = P.inst[P.qmode ? 0 : P.vinst[x]];
-        const int32_t lx = P.qmode ? -1 : (int32_t)(x - I.vbase);
-        const int4 xm = P.qmode ? P.qvmeta[x] : P.vmeta[x];
-        const int2 *xrow = (P.qmode ? P.qcrow : P.crow) + xm.x;
+        // query mode: item = (query, window), so the windows of a long query run on several
+        // CTAs at once instead of one after another
+        const int64_t x = QMODE ? it / P.qnw : (int64_t)P.items[it];
+        const int wq_item = QMODE ? (int)(it % P.qnw) : 0;
+        const InstDesc I = P.inst[QMODE ? 0 : P.vinst[x]];
+        const int32_t lx = QMODE ? -1 : (int32_t)(x - I.vbase);
+        const int4 xm = QMODE ? P.qvmeta[x] : P.vmeta[x];
+        const int2 *xrow = (QMODE ? P.qcrow : P.crow) + xm.x;
         const int32_t xl = xm.y;
-        const int32_t qs = f_remscore ? (P.qmode ? P.qqsplit[x] : P.qsplit[x]) : 0;
-        const float mwx = P.qmode ? P.qmw[x] : P.mw[x];
-        const float t = P.qmode ? P.qt : I.t;
+        const int32_t qs = f_remscore ? (QMODE ? P.qqsplit[x] : P.qsplit[x]) : 0;
+        const float mwx = QMODE ? P.qmw[x] : P.mw[x];
+        const float t = QMODE ? P.qt : I.t;
         const float beta = fmaxf(1e-5f, (float)(xl + 2) * 1.1920929e-7f);  // (|x|+2) * 2^-23
         // no component reaches remscore >= t: x can create no candidate at all
         if (f_remscore ? qs >= xl : xl == 0) continue;
@@ -240,8 +247,9 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
         }
         gsync(G, g, GT);
 
-        const int wfirst = (lx + 1) / I.W;
-        for (int w = wfirst; w < I.nw; w++) {
+        const int wfirst = QMODE ? wq_item : (lx + 1) / I.W;
+        const int wend = QMODE ? wq_item + 1 : I.nw;
+        for (int w = wfirst; w < wend; w++) {
             const int w0 = w * I.W;
             const int wn = min(I.W, I.n - w0);
             const int lo = max(0, lx + 1 - w0);
@@ -465,7 +473,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                 const int exw = warp_excl_scan_int(cw, lane, &tot);
                 if (lane < NW) wcnt[lane] = exw;
                 if (lane == 0) {
-                    const int64_t qw = P.qmode ? x * I.nw + w : I.qwbase + (int64_t)lx * I.nw + w;
+                    const int64_t qw = QMODE ? x * I.nw + w : I.qwbase + (int64_t)lx * I.nw + w;
                     P.cntq[qw] = tot;
                     int64_t b = 0, wr = 0;
                     if (tot > 0) {
@@ -481,7 +489,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                             Segment S;
                             S.src = b;
                             S.cnt = tot;
-                            S.i = P.qmode ? (int32_t)x : lx;
+                            S.i = QMODE ? (int32_t)x : lx;
                             P.segs[qw] = S;
                             wr = 1;
                         }
@@ -572,7 +580,7 @@ aps_status run_join_graph(aps_index *ix, JoinParams &P, int grid, int smem, unsi
         if (e == cudaSuccess) {
             cudaMemsetAsync(ctr, 0, ctr_bytes, cs);
             cudaMemsetAsync(cntq, 0, cnt_bytes, cs);
-            join_kernel<<<grid, JOIN_THREADS, smem, cs>>>(P);
+            join_kernel<false><<<grid, JOIN_THREADS, smem, cs>>>(P);
             cudaGraph_t g = nullptr;
             e = cudaStreamEndCapture(cs, &g);
             G.graph = g;
@@ -611,7 +619,7 @@ aps_status run_join_graph(aps_index *ix, JoinParams &P, int grid, int smem, unsi
         void *args[1] = {&P};
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof(kp));
-        kp.func = reinterpret_cast<void *>(join_kernel);
+        kp.func = reinterpret_cast<void *>(join_kernel<false>);
         kp.gridDim = dim3((unsigned)grid);
         kp.blockDim = dim3(JOIN_THREADS);
         kp.sharedMemBytes = (unsigned)smem;
@@ -644,7 +652,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     // the largest requirement of the four group shapes covers every launch
     int need = 0;
     for (int c = 0; c < 4; c++) need = std::max(need, group_bytes(Gs[c]) * Gs[c]);
-    APS_CUDA(cudaFuncSetAttribute(join_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
+    APS_CUDA(cudaFuncSetAttribute(join_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
 
     DBuf<int32_t> cntq;
     DBuf<unsigned long long> ctr;  // 0..4 counters, 5 stage count, 6 seg count, 8..11 work
@@ -695,6 +703,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
             P.work = ctr.p + 8;
             P.scratch = scratch.p;
             P.qmode = 0;
+            P.qnw = 1;
             APS_CUDA(cudaEventRecord(ev[0], s));
             APS_TRY(run_join_graph(ix, P, grid, smem, ctr.p, cntq.p, s));
         }
@@ -899,7 +908,7 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
     const int Gs[4] = {1, 2, 4, 8};
     int need = 0;
     for (int c = 0; c < 4; c++) need = std::max(need, group_bytes(Gs[c]) * Gs[c]);
-    APS_CUDA(cudaFuncSetAttribute(join_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
+    APS_CUDA(cudaFuncSetAttribute(join_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
     APS_CUDA(cudaMemsetAsync(ctr, 0, 16 * sizeof(unsigned long long), s));
     APS_CUDA(cudaMemsetAsync(cntq, 0, sizeof(int32_t) * nqw, s));
     if (ix->class_begin[4] > ix->class_begin[0]) {
@@ -928,7 +937,8 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
         P.work = ctr + 8;
         P.scratch = elists;
         P.qmode = 0;
-        join_kernel<<<grid, JOIN_THREADS, smem, s>>>(P);
+        P.qnw = 1;
+        join_kernel<false><<<grid, JOIN_THREADS, smem, s>>>(P);
         APS_LAUNCH_CHECK();
     }
     unsigned long long ch[16];
@@ -968,7 +978,7 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
     const int Gs[4] = {1, 2, 4, 8};
     int need = 0;
     for (int c = 0; c < 4; c++) need = std::max(need, group_bytes(Gs[c]) * Gs[c]);
-    APS_CUDA(cudaFuncSetAttribute(join_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
+    APS_CUDA(cudaFuncSetAttribute(join_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
     cudaEvent_t ev[3];
     for (int i = 0; i < 3; i++) APS_CUDA(cudaEventCreate(&ev[i]));
     struct EvGuard {
@@ -977,7 +987,8 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
             for (int i = 0; i < 3; i++) cudaEventDestroy(e[i]);
         }
     } evg{ev};
-    const int grid = (int)std::min<int64_t>(sms, std::max<int64_t>((nq + G - 1) / G, 1));
+    const int64_t nitems = nq * (int64_t)I.nw;  // (query, window) items
+    const int grid = (int)std::min<int64_t>(sms, std::max<int64_t>((nitems + G - 1) / G, 1));
     DBuf<int32_t> cntq;
     DBuf<unsigned long long> ctr;
     DBuf<int2> scratch, stage;
@@ -1002,7 +1013,7 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
             P.ncls = 1;
             P.cls_G[0] = G;
             P.cls_begin[0] = 0;
-            P.cls_begin[1] = nq;
+            P.cls_begin[1] = nitems;
             P.crow = d.crow.p;
             P.vmeta = d.vmeta.p;
             P.pnorm = d.pnorm.p;
@@ -1027,7 +1038,8 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
             P.qqsplit = qa.qsplit.p;
             P.qmw = qa.mw.p;
             P.qt = t;
-            join_kernel<<<grid, JOIN_THREADS, group_bytes(G) * G, s>>>(P);
+            P.qnw = std::max(I.nw, 1);
+            join_kernel<true><<<grid, JOIN_THREADS, group_bytes(G) * G, s>>>(P);
             APS_LAUNCH_CHECK();
         }
         APS_CUDA(cudaEventRecord(ev[1], s));
