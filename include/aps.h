@@ -253,9 +253,8 @@ typedef struct aps_tune_report {
 
 /* The size bucket (0 .. APS_TUNE_BUCKETS-1) of an instance of n vectors. */
 int32_t aps_tune_bucket(int64_t n);
-/* The built-in table. Self-joins: G = 8 up to 5120 vectors (one window), 4 up to 10240,
- * 2 above. Queryable indexes, whose queries visit every window: the largest G that keeps
- * the fewest windows (G = 1 above 20480 vectors). */
+/* The built-in table, the same in both columns: G = 8 up to 5120 vectors (one window),
+ * 4 up to 10240, 2 above. */
 void aps_tuning_default(aps_tuning *out);
 /* The table in force for this process. */
 void aps_get_tuning(aps_tuning *out);

@@ -24,10 +24,12 @@ const int GS[4] = {1, 2, 4, 8};
 // Default for self-joins: the largest G whose window still holds the whole instance (one
 // window per query), but at least 2 groups. Measured on the 200k-vector power-law set
 // (join ms): G = 1: 71.7, 2: 65.0, 4: 65.6, 8: 72.9.
-// Default for queryable indexes: a query visits every window of the index, so the fixed
-// cost per window dominates; the largest G that keeps the fewest windows. Measured on the
-// 1M-vector serving index (saturated queries/s): G = 1: 47,014, 2: 23,481, 4: 11,650.
-const aps_tuning DEFAULT_TUNING = {{8, 8, 8, 8, 4, 2, 2, 2}, {8, 8, 8, 8, 4, 2, 1, 1}};
+// Default for queryable indexes: the same. Their queries are (query, window) work items,
+// so a long query's windows run on several CTAs; on the 1M-vector serving index G = 1 and
+// G = 2 then serve alike (84.3k and 84.5k queries/s saturated). Before that split, a
+// batch waited for its longest query on one group, and G = 1 (a whole CTA per query)
+// served 47.0k against 23.5k with G = 2.
+const aps_tuning DEFAULT_TUNING = {{8, 8, 8, 8, 4, 2, 2, 2}, {8, 8, 8, 8, 4, 2, 2, 2}};
 
 std::mutex g_tune_mu;
 aps_tuning g_tune = DEFAULT_TUNING;
