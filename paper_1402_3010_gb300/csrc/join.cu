@@ -662,6 +662,20 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     // that still overflows is re-run with room for what it reserved plus one slab per
     // group. Segments are stored per (vector, window) slot, so their table never overflows.
     int64_t stage_cap = std::max<int64_t>({ix->hint_pairs, g_stage_hint.load(), (int64_t)1 << 20, ix->nnz});
+    if (ix->hint_pairs == 0 && g_stage_hint.load() == 0) {
+        // no join of this process has sized the staging yet: take room for every possible
+        // pair plus one slab per group, but at most an eighth of the free device memory
+        // and 2^28 pairs, so that a first join rarely has to run twice
+        int64_t most = (int64_t)sms * 8 * JOIN_STAGE_SLAB;
+        for (const InstDesc &I : ix->inst_h) most += (int64_t)I.n * (I.n - 1) / 2;
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+            const int64_t room = std::min<int64_t>({most, (int64_t)(fr / 8 / sizeof(int2)), (int64_t)1 << 28});
+            stage_cap = std::max(stage_cap, room);
+        } else {
+            cudaGetLastError();
+        }
+    }
     if (const int64_t once = g_stage_cap_once.exchange(0); once > 0) stage_cap = once;
     DBuf<int2> stage;
     DBuf<Segment> segs;
