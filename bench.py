@@ -36,7 +36,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "similarity evaluations/s"
 UNIT = "pair-evaluations/s"
-WORKLOAD = "large sparse all-pairs: n=200000, m=100000, |x| power law (alpha=1.4135, mean 50, max 2000), Zipf(1.0) ids, log-normal(0,1) weights, L2-normalised, FP32"
+WORKLOAD = ("large sparse all-pairs: n=200000, m=100000, |x| power law (alpha=1.4135, mean 50, max 2000), "
+            "Zipf(1.0) ids, log-normal(0,1) weights, L2-normalised, FP32")
 
 
 def parse():
@@ -61,7 +62,8 @@ def parse():
                     help="the same for indexes built to answer queries (the serving index); default: the library's")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched workload: time the default tile table instead of the autotuned one")
-    ap.add_argument("--workload", default="sparse", choices=["sparse", "dense", "batched", "serving", "ablation", "graph", "horizontal", "vertical"],
+    ap.add_argument("--workload", default="sparse",
+                    choices=["sparse", "dense", "batched", "serving", "ablation", "graph", "horizontal", "vertical"],
                     help="sparse: the 200k-vector sparse self-join (default line); dense: the 200k x 256 "
                          "embedding self-join on the tensor cores; batched: 512 independent sparse "
                          "instances; serving: query batches against a 1M-vector resident index")
@@ -1028,7 +1030,8 @@ def run_horizontal(args, rank, world):
         if x.is_alive():
             x.kill()
     if len(infos) < p:
-        return {"metric": METRIC, "value": None, "unit": UNIT, "error": f"{p - len(infos)} of {p} ranks returned nothing"}
+        return {"metric": METRIC, "value": None, "unit": UNIT,
+                "error": f"{p - len(infos)} of {p} ranks returned nothing"}
     secs = max(x["seconds"] for x in infos)
     root = [x for x in infos if x["rank"] == 0][0]
     part_bytes = {x["rank"]: x["part_bytes"] for x in infos}
