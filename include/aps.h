@@ -270,7 +270,9 @@ aps_status aps_set_tuning(const aps_tuning *tuning);
  * is. The winner is installed
  * (aps_set_tuning) and returned in *out; *report (may be NULL) gets the measurements.
  * APS_QUERYABLE and APS_HOST_OUTPUT in flags are ignored (the self-join column is tuned).
- * Results of the batch do not depend on the table; only the join time does. */
+ * Results of the batch do not depend on the table; only the join time does.
+ * Errors: APS_EINVAL (arguments or rows, as aps_batch_all_pairs_csr), APS_ENOMEM,
+ * APS_ECUDA; on any error the table in force is left unchanged. */
 aps_status aps_autotune_batch_csr(int32_t k, const int64_t *row_offsets, const int64_t *indptr,
                                   const int32_t *idx, const float *val, const int32_t *m,
                                   const float *t, uint32_t flags, void *stream, aps_tuning *out,
