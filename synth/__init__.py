@@ -6,7 +6,7 @@ deterministic for a given seed (NumPy PCG64).
 
 The paper's own datasets (radikal, 20-newsgroups, wikipedia, facebook, virginia-tech;
 Sec. 7, Table 1) are not available, so these shapes stand in for them. They keep the
-property the paper stresses (Sec. 7.2): dimension density follows a power law, so a
+property the paper stresses (Sec. 7.3): dimension density follows a power law, so a
 few dense dimensions dominate the work of the inverted-index join.
 
 Sparse matrices are returned as CSR in canonical input form: int64 ``indptr[n+1]``,
