@@ -984,7 +984,7 @@ def _horizontal_rank(rank, p, port, n, m, t, out_q):
 
 
 def run_horizontal(args, rank, world):
-    """§8 row f4: the horizontal driver (Sec. 5.2, Alg. 6) with --ranks host processes
+    """The horizontal driver (Sec. 5.2, Alg. 6) with --ranks host processes
     on this machine's GPU(s), against the single-process join of the same workload."""
     import multiprocessing as mp
     import socket
@@ -1061,7 +1061,7 @@ def run_horizontal(args, rank, world):
 
 
 def run_vertical(args, rank, world):
-    """§8 row f2: the vertical algorithm with local pruning (Sec. 5.1, Lemma 1, Eq. 1) for
+    """The vertical algorithm with local pruning (Sec. 5.1, Lemma 1, Eq. 2) for
     each block count in --blocks: p block joins at t/p on the GPU, the union completed
     exactly (aps_pairs_verify), checked against the plain join of the same workload."""
     import torch

@@ -312,7 +312,7 @@ void aps_graph_free(aps_graph *g);
 
 /* ---- exact verification of candidate pairs --------------------------------------- */
 /* The score merge of the vertical algorithm with local pruning (Sec. 5.1, Lemma 1 and
- * Eq. 1: a match has a partial score >= t/p on at least one of p dimension blocks): the
+ * Eq. 2: a match has a partial score >= t/p on at least one of p dimension blocks): the
  * union of k candidate lists `lists[0..k)` (pairs i < j of the same n vectors, device or
  * host results, any order, duplicates allowed) is deduplicated, each pair's dot product is
  * recomputed in float64 from the rows of the CSR (indptr/idx/val as for aps_build_index,

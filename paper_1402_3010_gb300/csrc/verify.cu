@@ -1,5 +1,5 @@
 // Exact verification of candidate pairs: the score merge of the vertical algorithm with
-// local pruning (Sec. 5.1, Lemma 1 / Eq. 1). The candidates of p dimension blocks (pairs
+// local pruning (Sec. 5.1, Lemma 1 / Eq. 2). The candidates of p dimension blocks (pairs
 // whose partial score on some block reached t/p) are united, and each pair's full dot
 // product is recomputed from the rows and compared with t.
 //

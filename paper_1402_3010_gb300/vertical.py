@@ -1,5 +1,5 @@
 """Vertical (dimension-partitioned) All-Pairs with local pruning, after Sec. 5.1
-(Par-All-Pairs-0-Vert, Lemma 1 and Eq. 1).
+(Par-All-Pairs-0-Vert, Lemma 1 and Eq. 2).
 
 The dimensions are split into p blocks; the join of each block's projection of the
 vectors (the vectors restricted to that block's dimensions) at the local threshold
@@ -50,7 +50,7 @@ def project(indptr, idx, val, block, k: int):
 
 
 def local_threshold(t: float, p: int) -> float:
-    """t/p (Eq. 1), lowered by a relative 1e-6 and rounded down to float32, so that the
+    """t/p (Eq. 2), lowered by a relative 1e-6 and rounded down to float32, so that the
     float rounding of the local scores can never hide a block that reaches t/p."""
     tl = np.float32(t / p * (1.0 - 1e-6))
     if float(tl) > t / p * (1.0 - 1e-6):

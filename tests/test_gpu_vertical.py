@@ -1,4 +1,4 @@
-"""GPU parity of the vertical algorithm with local pruning (Sec. 5.1, Lemma 1, Eq. 1):
+"""GPU parity of the vertical algorithm with local pruning (Sec. 5.1, Lemma 1, Eq. 2):
 the exact candidate merge (aps_pairs_verify) against the oracle's float64 dots, and the
 whole vertical join against the oracle's brute force for several block counts; plus the
 sub-unit-norm join the blocks run on."""
