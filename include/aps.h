@@ -141,26 +141,33 @@ aps_status aps_build_index(const int64_t *indptr, const int32_t *idx, const floa
  * flags: APS_NO_MINSIZE / APS_NO_REMSCORE / APS_NO_UPPERBOUND ablations and
  * APS_HOST_OUTPUT. Result buffers are allocated by the library; free with aps_pairs_free.
  * The first call on an index captures its join phase as a CUDA graph that later calls
- * replay; calls on one index must not overlap each other (aps_query may run meanwhile). */
+ * replay; calls on one index must not overlap each other (aps_query may run meanwhile).
+ * Errors: APS_EINVAL (NULL arguments or a batched index), APS_ENOMEM, APS_ECUDA,
+ * APS_EOVERFLOW (the staging still overflowed after growing twice); *out is then empty. */
 aps_status aps_all_pairs(aps_index *index, uint32_t flags, aps_pairs *out);
 
 /* Match nq external query vectors (CSR as in aps_build_index) against the index
  * (the local matching step of the horizontal algorithm, Alg. 6): every (q, y) with
  * dot(q, y) >= t, as i = query row, j = vector id, sorted by (i, j). The index must
- * have been built with APS_QUERYABLE, and t >= the build threshold. */
+ * have been built with APS_QUERYABLE, and t >= the build threshold.
+ * Errors: APS_EINVAL (NULL arguments, an index not single-instance or not built with
+ * APS_QUERYABLE, t outside [build threshold, 1], malformed query rows), APS_ENOMEM,
+ * APS_ECUDA, APS_EOVERFLOW; *out is then empty. */
 aps_status aps_query(aps_index *index, const int64_t *qptr, const int32_t *qidx,
                      const float *qval, int32_t nq, float t, uint32_t flags, aps_pairs *out);
 
 /* Read back the index build results for verification of each step. Any pointer may be
  * NULL. Host arrays, caller-allocated, sizes: len/mw/split/qsplit/mw_pre [n],
  * rank_of_dim/nnz_d/mw_d [m], crank/cval [nnz] (components re-ordered by rank, the
- * CSR row pointers are the input's), list_ptr [m+1] (by rank), post_id/post_w [list_ptr[m]]. */
+ * CSR row pointers are the input's), list_ptr [m+1] (by rank), post_id/post_w [list_ptr[m]].
+ * Errors: APS_EINVAL (NULL index), APS_ECUDA. */
 aps_status aps_index_export(const aps_index *index, int32_t *len, float *mw, int32_t *nnz_d,
                             float *mw_d, int32_t *rank_of_dim, int32_t *crank, float *cval,
                             int32_t *split, int32_t *qsplit, float *mw_pre, int64_t *list_ptr,
                             int32_t *post_id, float *post_w);
 
-/* Sizes of the index: n, m, nnz and the number of indexed components. */
+/* Sizes of the index: n, m, nnz and the number of indexed components (any pointer may
+ * be NULL). Errors: APS_EINVAL (NULL index). */
 aps_status aps_index_info(const aps_index *index, int32_t *n, int32_t *m, int64_t *nnz,
                           int64_t *indexed);
 
@@ -183,7 +190,8 @@ aps_status aps_index_info(const aps_index *index, int32_t *n, int32_t *m, int64_
 aps_status aps_all_pairs_noalloc(aps_index *index, int32_t *i, int32_t *j, float *score,
                                  int64_t capacity, int64_t *count, void *stream);
 
-/* Counters and timings of the last join on this index (see aps_stats). */
+/* Counters and timings of the last join or query batch on this index (see aps_stats).
+ * Errors: APS_EINVAL (NULL index or out). */
 aps_status aps_index_stats(const aps_index *index, aps_stats *out);
 
 void aps_index_free(aps_index *index);
@@ -192,7 +200,7 @@ void aps_index_free(aps_index *index);
 void aps_pairs_free(aps_pairs *pairs);
 
 /* Copy a result's arrays into caller-owned buffers (host or device; any may be NULL) on
- * `stream`, and wait for the copies. */
+ * `stream`, and wait for the copies. Errors: APS_EINVAL (NULL pairs), APS_ECUDA. */
 aps_status aps_pairs_copy_to(const aps_pairs *pairs, int32_t *i, int32_t *j, float *score,
                              void *stream);
 
@@ -211,7 +219,9 @@ typedef struct aps_instance {
  * shapes from the table of aps_set_tuning / aps_autotune_batch_csr). outs[k] receives
  * instance k's pairs (i < j, local row ids, sorted); all k results share one allocation,
  * released by calling aps_pairs_free on every element. stats (may be NULL) gets the
- * totals. */
+ * totals. Errors: APS_EINVAL (k < 1, NULL arrays, an instance with n < 0, m < 1, t
+ * outside (0, 1] or malformed rows), APS_ENOMEM, APS_ECUDA, APS_EOVERFLOW; every
+ * outs[r] is then empty. */
 aps_status aps_batch_all_pairs(int32_t k, const aps_instance *inst, uint32_t flags,
                                void *stream, aps_pairs *outs, aps_stats *stats);
 
@@ -220,7 +230,8 @@ aps_status aps_batch_all_pairs(int32_t k, const aps_instance *inst, uint32_t fla
  * indptr (row_offsets[k]+1 entries, global: indptr[0] = 0), idx, val as in
  * aps_build_index (device pointers with APS_DEVICE_PTRS, dimension ids local to each
  * instance, in [0, m[r])); m and t are host arrays of k entries. Results and ownership as
- * in aps_batch_all_pairs. Avoids per-instance copies when the batch is device-resident. */
+ * in aps_batch_all_pairs. Avoids per-instance copies when the batch is device-resident.
+ * Errors as aps_batch_all_pairs (also row_offsets[0] != 0). */
 aps_status aps_batch_all_pairs_csr(int32_t k, const int64_t *row_offsets, const int64_t *indptr,
                                    const int32_t *idx, const float *val, const int32_t *m,
                                    const float *t, uint32_t flags, void *stream, aps_pairs *outs,
@@ -254,7 +265,7 @@ typedef struct aps_tune_report {
 /* The size bucket (0 .. APS_TUNE_BUCKETS-1) of an instance of n vectors. */
 int32_t aps_tune_bucket(int64_t n);
 /* The built-in table, the same in both columns: G = 8 up to 5120 vectors (one window),
- * 4 up to 10240, 2 above. */
+ * 4 up to 10240, 2 above. (This and aps_get_tuning ignore a NULL out.) */
 void aps_tuning_default(aps_tuning *out);
 /* The table in force for this process. */
 void aps_get_tuning(aps_tuning *out);
@@ -283,7 +294,12 @@ aps_status aps_autotune_batch_csr(int32_t k, const int64_t *row_offsets, const i
  * the S = D.D^T view of Sec. 2.1 computed as a BF16 tensor-core product with float32
  * accumulation, a provable margin delta below t for candidates, float32 rescoring of
  * the candidates from X, float64 inside the band, sorted by (i, j). d must be a
- * multiple of 64 and at most 512. Needs an sm_103a device. */
+ * multiple of 64 and at most 512. Needs an sm_103a device.
+ * Errors: APS_EINVAL (d not a multiple of 64 in [64, 512], t outside (0, 1], a row whose
+ * norm is off by more than 1e-3 without APS_NORMALIZE, a zero or non-finite row),
+ * APS_EUNSUPPORTED (no sm_103 device, or no tensor-map encoder in the driver),
+ * APS_ETIMEOUT (a pipeline wait of the tensor-core kernel ran out; the context stays
+ * usable), APS_ENOMEM, APS_ECUDA; *out is then empty. */
 aps_status aps_all_pairs_dense(const float *X, int32_t n, int32_t d, float t, uint32_t flags,
                                void *stream, aps_pairs *out, aps_stats *stats);
 
@@ -302,11 +318,14 @@ aps_status aps_graph_csr(const int32_t *i, const int32_t *j, const float *s, int
  * similarity graph, Sec. 2.2): row v of nbr[n * k] / wk[n * k] holds v's neighbours of
  * largest weight, ties by smaller id, in that order; rows with fewer than k neighbours
  * end in id -1, weight 0. nbr and wk are caller buffers, device pointers with
- * APS_DEVICE_PTRS and host pointers otherwise. 1 <= k <= 256. */
+ * APS_DEVICE_PTRS and host pointers otherwise. 1 <= k <= 256.
+ * Errors: APS_EINVAL (not a device graph from aps_graph_csr, k out of range, NULL
+ * outputs), APS_ENOMEM, APS_ECUDA. */
 aps_status aps_graph_knn(const aps_graph *g, int32_t k, int32_t *nbr, float *wk, uint32_t flags,
                          void *stream);
 /* Copy a graph's arrays (device or host) into caller buffers of n + 1 / nnz / nnz
- * elements (any of them may be NULL). Synchronous. */
+ * elements (any of them may be NULL). Synchronous. Errors: APS_EINVAL (a graph not from
+ * aps_graph_csr), APS_ECUDA. */
 aps_status aps_graph_copy_to(const aps_graph *g, int64_t *row_ptr, int32_t *col, float *w, void *stream);
 void aps_graph_free(aps_graph *g);
 
@@ -338,18 +357,29 @@ typedef struct aps_query_req {
 /* A request loop over a device-resident APS_QUERYABLE index. Submitted query batches
  * are admitted in arrival order when one of `slots` execution slots is free and their
  * estimated device footprint fits in mem_budget bytes; admitted batches run
- * concurrently on separate streams (continuous batching). */
+ * concurrently on separate streams (continuous batching). The server borrows the index
+ * until aps_server_free. Errors: APS_EINVAL (NULL arguments, slots outside [1, 64], an
+ * index not single-instance or not built with APS_QUERYABLE), APS_ECUDA. */
 aps_status aps_server_create(aps_index *index, size_t mem_budget, int32_t slots,
                              aps_server **out);
+/* Queue a query batch; its rows are copied, so the request's arrays may be reused on
+ * return. *ticket identifies it for poll and cancel. Errors: APS_EINVAL (NULL
+ * arguments, malformed rows, t outside [build threshold, 1]). */
 aps_status aps_stream_submit(aps_server *server, const aps_query_req *req, uint64_t *ticket);
 /* Wait up to timeout_us (0 = just check) for a ticket. APS_EAGAIN if not done yet; on
- * APS_OK `out` receives the pairs (host memory) and the ticket is retired. */
+ * APS_OK `out` receives the pairs (host memory) and the ticket is retired. Errors:
+ * APS_EINVAL (NULL arguments, an unknown or retired ticket), APS_ECANCELED (cancelled;
+ * the ticket is retired), or the batch's own error status (the ticket is retired). */
 aps_status aps_stream_poll(aps_server *server, uint64_t ticket, int32_t timeout_us,
                            aps_pairs *out);
+/* Cancel a ticket: a queued batch never runs, a running one completes and its result is
+ * dropped; the next poll returns APS_ECANCELED. Errors: APS_EINVAL (NULL server, an
+ * unknown ticket). */
 aps_status aps_stream_cancel(aps_server *server, uint64_t ticket);
 void aps_server_free(aps_server *server);
 
 /* ---- misc ----------------------------------------------------------------------- */
+/* The message of this thread's last failed call (empty if none). */
 const char *aps_last_error(void);
 const char *aps_version(void);
 
