@@ -52,3 +52,27 @@ def test_set_and_get_round_trip_and_validation(A):
     A.aps_set_tuning(A.aps_tuning_default(), A.aps_tuning_default(query=True))
     assert A.aps_get_tuning() == A.aps_tuning_default()
     assert A.aps_get_tuning(query=True) == A.aps_tuning_default(query=True)
+
+
+def test_autotuner_rejects_bad_batches_before_any_gpu_work(A):
+    """Argument checks run on the host before anything touches the device: an empty
+    batch, row offsets not starting at 0, m < 1 and t outside (0, 1] are APS_EINVAL,
+    and the table in force is unchanged."""
+    import numpy as np
+
+    before = A.aps_get_tuning()
+    ip = np.array([0, 1, 2], dtype=np.int64)
+    ix = np.array([0, 1], dtype=np.int32)
+    vv = np.ones(2, dtype=np.float32)
+    cases = [
+        (np.array([0], dtype=np.int64), [5], [0.5]),          # k = 0
+        (np.array([1, 2], dtype=np.int64), [5], [0.5]),       # row_offsets[0] != 0
+        (np.array([0, 2], dtype=np.int64), [0], [0.5]),       # m < 1
+        (np.array([0, 2], dtype=np.int64), [5], [1.5]),       # t > 1
+        (np.array([0, 2], dtype=np.int64), [5], [0.0]),       # t = 0
+    ]
+    for ro, m, t in cases:
+        with pytest.raises(A.APSError) as e:
+            A.aps_autotune_batch_csr(ro, ip, ix, vv, np.array(m, np.int32), np.array(t, np.float32))
+        assert e.value.status == A.EINVAL
+    assert A.aps_get_tuning() == before
