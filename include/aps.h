@@ -182,11 +182,16 @@ aps_status aps_index_info(const aps_index *index, int32_t *n, int32_t *m, int64_
  * join uses at most 32 CTAs. Limits: the index's (vector, window) slots must fit the
  * arena with room left to stage pairs (else APS_EINVAL, before any work), and the pairs
  * must fit both the staging room and `capacity` (else APS_EOVERFLOW with *count = the
- * number of pairs). The first call on a device looks up the array's device address
- * (once per device, with that device current); make that first call before any stream
- * capture. Every call shares the one array and keeps no state in it between calls, but
- * calls that overlap on the GPU (other streams, other host threads) race on it: run them
- * one at a time per device. Calls no cudaMalloc/cudaFree or allocating routine. */
+ * number of pairs). The current device must be the index's device, and i, j and score
+ * must be device memory of that device (else APS_EINVAL). The first call on a device
+ * looks up the array's device address (once per device, with that device current).
+ * Every call reads its counters back and synchronizes `stream` before it returns, so it
+ * must not be called while `stream` (or the legacy default stream it may wait on) is
+ * being captured into a CUDA graph. Every call shares the one array and keeps no state in
+ * it between calls, but calls that overlap on the GPU (other streams, other host threads)
+ * race on it: run them one at a time per device. The index's stats (aps_index_stats)
+ * then report this join's counters, with zero timings. Calls no cudaMalloc/cudaFree or
+ * allocating routine. */
 aps_status aps_all_pairs_noalloc(aps_index *index, int32_t *i, int32_t *j, float *score,
                                  int64_t capacity, int64_t *count, void *stream);
 

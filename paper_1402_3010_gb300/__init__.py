@@ -282,6 +282,17 @@ def aps_all_pairs_noalloc(index: int, i, j, score, stream=None) -> int:
     """Self-join into caller-owned CUDA int32/int32/float32 tensors of equal length (the
     capacity), with no allocation inside the library; returns the number of pairs.
     APSError with status EOVERFLOW carries the needed count in .count."""
+    # The kernels write these arrays from the device: anything but contiguous CUDA tensors
+    # of the right type (a NumPy array, a CPU tensor, int16 or a strided view) would make
+    # them write to host memory or past the caller's storage.
+    for a, dt, nm in ((i, "int32", "i"), (j, "int32", "j"), (score, "float32", "score")):
+        if not _is_torch(a) or not a.is_cuda:
+            raise ValueError(f"{nm} must be a CUDA tensor (got {type(a).__name__})")
+        if str(a.dtype) != f"torch.{dt}" or not a.is_contiguous():
+            raise ValueError(f"{nm} must be a contiguous {dt} CUDA tensor (got {a.dtype}, "
+                             f"contiguous={a.is_contiguous()})")
+    if not (i.device == j.device == score.device):
+        raise ValueError("i, j and score must be on the same CUDA device")
     cap = int(i.numel())
     if int(j.numel()) != cap or int(score.numel()) != cap:
         raise ValueError("i, j and score must have the same length")

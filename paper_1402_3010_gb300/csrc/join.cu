@@ -7,13 +7,16 @@
 // windows because n floats do not fit on chip). For a query x (a whole vector of the set, taken
 // from a cost-ordered work list) and each window of candidates y > x:
 //   1. accumulate: A[y] += x[i] * y[i] over the posting lists of x's components,
-//      first over the components with remscore >= t (these may create candidates, and
-//      mark each touched slot in a bitmap), then over the rest, which only update
-//      candidates that exist (remscore); entries with |y| below minsize are skipped using
-//      the size class stored in the entry. Lists are in id order, so a warp's 32 lanes add
-//      into 32 increasing slots;
-//   2. verify: each warp walks its share of the bitmap and takes the marked slots in
-//      order, one candidate per lane: A[y] + ||y'||_2 < t rejects cheaply, then the
+//      first over the components with remscore >= t (these may create candidates), then
+//      over the rest, which only update candidates that exist (remscore); entries with |y|
+//      below minsize are skipped using the size class stored in the entry. A holds 32-bit
+//      fixed-point sums (products rounded to multiples of 2^-30, a creating product at
+//      least one unit), so its updates are native integer shared-memory atomics and a
+//      slot is a candidate exactly when it is non-zero. Lists are in id order, so a
+//      warp's 32 lanes add into 32 increasing slots;
+//   2. verify: each warp scans its share of A 32 slots at a time (a ballot of the
+//      non-zero slots is one 32-bit word of candidates) and takes the candidates in slot
+//      order, one per lane: A[y] + ||y'||_2 < t rejects cheaply, then the
 //      upperbound test A[y] + min(|y'|, |x|) * maxweight(x) * maxweight(y') >= t, then
 //      s = A[y] + dot(x, y') with y' the unindexed prefix of y; scores within a band of
 //      t are recomputed in float64 and decided there;
@@ -82,7 +85,6 @@ __host__ __device__ constexpr int group_bytes(int G) {
            + 4 * (JOIN_THREADS / G + 4)              // c_ch0
            + 4 * (JOIN_THREADS / G)                  // c_xv
            + 4 * (JOIN_RMAX / G)                     // xtab
-           + 4 * (JOIN_WMAX / G / 32)                // touched-slot bitmap
            + 8 * (JOIN_XCAP / G)                     // x's row
            + 8 * 32                                  // wsum
            + 4 * 32                                  // wcnt
@@ -184,14 +186,13 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     const int lane = gt & 31, gw = gt >> 5, NW = GT >> 5;
     const int WG = JOIN_WMAX / G, RG = JOIN_RMAX / G;
     unsigned char *base = smem + (size_t)g * group_bytes(G);
-    float *A = reinterpret_cast<float *>(base);
+    uint32_t *A = reinterpret_cast<uint32_t *>(base);  // fixed point, units of 2^-30
     int64_t *c_start = reinterpret_cast<int64_t *>(A + WG);        // [GT]
     int32_t *c_cnt = reinterpret_cast<int32_t *>(c_start + GT);    // [GT]
     int32_t *c_ch0 = c_cnt + GT;                                    // [GT + 4] chunk prefix
     float *c_xv = reinterpret_cast<float *>(c_ch0 + GT + 4);        // [GT]
     float *xtab = c_xv + GT;                                        // [RG]
-    uint32_t *bm = reinterpret_cast<uint32_t *>(xtab + RG);        // [WG / 32]
-    int2 *xr = reinterpret_cast<int2 *>(bm + WG / 32);
+    int2 *xr = reinterpret_cast<int2 *>(xtab + RG);
     const int XG = JOIN_XCAP / G;
     int64_t *wsum = reinterpret_cast<int64_t *>(xr + XG);
     int32_t *wcnt = reinterpret_cast<int32_t *>(wsum + 32);
@@ -199,8 +200,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     int2 *elist = P.scratch + ((size_t)blockIdx.x * NWARPS + (threadIdx.x >> 5)) * JOIN_ECAP;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    for (int i = gt; i < WG; i += GT) A[i] = 0.f;
-    for (int i = gt; i < WG / 32; i += GT) bm[i] = 0u;
+    for (int i = gt; i < WG; i += GT) A[i] = 0u;
     if (gt == 0) bc[3] = bc[4] = bc[5] = 0;  // this group's staging slab: base, used, size
 
     for (;;) {
@@ -320,16 +320,17 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                         }
                         cc = a;
                     }
+                    // x's value scaled by 2^30 (exact): products convert straight to A's units
                     int64_t cst = c_start[cc], cen = cst + c_cnt[cc];
                     int cch0 = c_ch0[cc];
-                    float cxv = c_xv[cc];
+                    float cxv = c_xv[cc] * 1073741824.f;
                     for (; ch < che; ch++) {
                         if (ch >= c_ch0[cc + 1]) {
                             cc++;
                             cst = c_start[cc];
                             cen = cst + c_cnt[cc];
                             cch0 = c_ch0[cc];
-                            cxv = c_xv[cc];
+                            cxv = c_xv[cc] * 1073741824.f;
                         }
                         const int64_t e0 = cst + (int64_t)(ch - cch0) * 128 + lane;
                         int2 ent[4];
@@ -342,12 +343,13 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                             if ((uint32_t)ent[u].x < smin_tag) continue;  // minsize
                             const int slot = (ent[u].x & idmask) - w0;
                             if (slot < lo) continue;
-                            const float prod = cxv * __int_as_float(ent[u].y);
+                            // x[i] * y[i] in units of 2^-30, rounded to nearest; a creating
+                            // product is at least one unit so that its slot becomes non-zero
+                            const uint32_t q = __float2uint_rn(__fmul_rn(cxv, __int_as_float(ent[u].y)));
                             if (phase == 0) {
-                                atomicAdd(&A[slot], prod);
-                                atomicOr(&bm[slot >> 5], 1u << (slot & 31));
-                            } else if (A[slot] != 0.f) {
-                                atomicAdd(&A[slot], prod);
+                                atomicAdd(&A[slot], q + (q == 0u));
+                            } else if (A[slot] != 0u) {
+                                atomicAdd(&A[slot], q);
                             }
                         }
                     }
@@ -355,21 +357,22 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                 gsync(G, g, GT);
             }
             if (!created) continue;  // no candidate can exist in this window
-            // ---------------- verify. The creating pass set one bit of bm per touched slot.
-            // Each warp walks its share of bm 32 words (1024 slots) at a time and takes the
-            // set bits in slot order, 32 candidates per batch: lane j of a batch takes the
-            // candidate at position b + j, located from the lanes' popcount prefix. Taken
-            // slots are cleared in A (bm words as they are read), and the emitted (y, score)
-            // go to the warp's scratch list in increasing y.
+            // ---------------- verify. A slot is a candidate when A is non-zero. Each warp
+            // scans its share of A 1024 slots at a time: word k of the 32 (a ballot of the
+            // non-zero slots among 32) goes to lane k. The set bits are taken in slot order,
+            // 32 candidates per batch: lane j of a batch takes the candidate at position
+            // b + j, located from the lanes' popcount prefix. Taken slots are cleared in A,
+            // and the emitted (y, score) go to the warp's scratch list in increasing y.
             const int wlo = lo >> 5, whi = (wn + 31) >> 5;
             const int wper = (whi - wlo + NW - 1) / NW;
             const int wb = wlo + gw * wper, we = min(wb + wper, whi);
             int ne = 0;
             for (int wq = wb; wq < we; wq += 32) {
                 uint32_t word = 0u;
-                if (wq + lane < we) {
-                    word = bm[wq + lane];
-                    bm[wq + lane] = 0u;
+                const int nwd = min(32, we - wq);
+                for (int k = 0; k < nwd; k++) {
+                    const uint32_t b = __ballot_sync(0xffffffffu, A[((wq + k) << 5) + lane] != 0u);
+                    if (lane == k) word = b;
                 }
                 const int c = __popc(word);
                 int T;
@@ -394,8 +397,8 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     if (have) {
                         for (int k = p - oex; k > 0; k--) ow &= ow - 1u;
                         s = ((wq + own) << 5) + (__ffs(ow) - 1);
-                        v = A[s];
-                        A[s] = 0.f;
+                        v = __uint2float_rn(A[s]) * 9.31322574615478515625e-10f;  // 2^-30
+                        A[s] = 0u;
                         const int64_t gy = I.vbase + w0 + s;
                         sc = v;
                         // dot(x, y') <= ||y'||_2: most candidates stop here, on a 4-byte load
@@ -977,6 +980,19 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
         APS_LAUNCH_CHECK();
     }
     APS_CUDA(cudaStreamSynchronize(s));
+    // the index's stats report the last join, whichever entry point ran it (no timings:
+    // this path records no events)
+    std::lock_guard<std::mutex> lk(ix->stats_mu);
+    aps_stats &S = ix->stats;
+    S.visits = (int64_t)ch[0];
+    S.candidates = (int64_t)ch[1];
+    S.verified = (int64_t)ch[2];
+    S.pairs = (int64_t)ch[3];
+    S.band = (int64_t)ch[4];
+    S.reruns = 0;
+    S.ms_join = S.ms_sort = S.ms_total = 0.f;
+    S.evaluations = 0;
+    for (const InstDesc &I : ix->inst_h) S.evaluations += (int64_t)I.n * (I.n - 1) / 2;
     return APS_OK;
 }
 

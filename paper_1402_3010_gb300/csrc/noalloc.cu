@@ -25,10 +25,8 @@ __device__ __align__(256) unsigned char g_arena[kArenaBytes];
 std::mutex g_mu;
 void *g_arena_dev[256];
 
-aps_status arena_address(void **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return aps::cuda_status(e, "cudaGetDevice", __FILE__, __LINE__);
+aps_status arena_address(int dev, void **out) {
+    cudaError_t e;
     if (dev < 0 || dev >= 256) {
         aps::set_error("device ordinal %d out of range", dev);
         return APS_EINVAL;
@@ -61,8 +59,34 @@ extern "C" aps_status aps_all_pairs_noalloc(aps_index *index, int32_t *i, int32_
         aps::set_error("aps_all_pairs_noalloc needs a single-instance index");
         return APS_EINVAL;
     }
+    // The arena used is the current device's; the index's arrays live on index->device.
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return aps::cuda_status(e, "cudaGetDevice", __FILE__, __LINE__);
+    if (dev != index->device) {
+        aps::set_error("the current device (%d) is not the index's device (%d)", dev, index->device);
+        return APS_EINVAL;
+    }
+    // The output arrays are written by kernels: they must be device memory of this device
+    // (a host pointer would fault or, where the GPU can reach host memory, write there).
+    if (capacity > 0) {
+        const void *outs[3] = {i, j, score};
+        for (const void *q : outs) {
+            cudaPointerAttributes pa;
+            e = cudaPointerGetAttributes(&pa, q);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                aps::set_error("output array %p is not CUDA memory", q);
+                return APS_EINVAL;
+            }
+            if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != dev) {
+                aps::set_error("output array %p is not device memory of device %d", q, dev);
+                return APS_EINVAL;
+            }
+        }
+    }
     void *arena = nullptr;
-    APS_TRY(arena_address(&arena));
+    APS_TRY(arena_address(dev, &arena));
     return aps::join_noalloc(index, static_cast<unsigned char *>(arena), kArenaBytes, kMaxCtas, i, j, score,
                              capacity, count, static_cast<cudaStream_t>(stream));
 }

@@ -2,18 +2,28 @@
 
 Acceptance: pairs sorted by (i, j) with i < j (self-joins), identical pair sets except
 pairs whose float64 score lies within `band` of t, and float32 scores within `tol` of
-the float64 score."""
+the float64 score. A pair only the CUDA path reports is judged by its float64 score,
+recomputed here from the inputs (never by the score the CUDA path returned): the caller
+names the inputs with `csr=` (rows of a self-join, or the indexed set of a query result
+together with `queries=`) or `dense=` (the rows of a dense self-join)."""
 import numpy as np
 
 
-def row_dot64(c, a, b):
-    ia, va = c.row(int(a))
+def row_dot64(c, a, b, q=None):
+    """float64 dot product of row a of q (default: of c) with row b of c."""
+    ia, va = (q if q is not None else c).row(int(a))
     ib, vb = c.row(int(b))
     common, pa, pb = np.intersect1d(ia, ib, assume_unique=True, return_indices=True)
     return float(np.dot(va[pa].astype(np.float64), vb[pb].astype(np.float64)))
 
 
-def compare(i, j, s, ref, t, n, *, band=1e-5, tol=1e-5, self_join=True, csr=None):
+def dense_dot64(X, a, b):
+    return float(np.dot(X[int(a)].astype(np.float64), X[int(b)].astype(np.float64)))
+
+
+def compare(i, j, s, ref, t, n, *, band=1e-5, tol=1e-5, self_join=True, csr=None, queries=None, dense=None):
+    if csr is None and dense is None:
+        raise ValueError("compare() needs the inputs (csr= or dense=) to recompute extra pairs in float64")
     i = np.asarray(i, np.int64)
     j = np.asarray(j, np.int64)
     s = np.asarray(s, np.float64)
@@ -29,8 +39,8 @@ def compare(i, j, s, ref, t, n, *, band=1e-5, tol=1e-5, self_join=True, csr=None
         assert abs(rmap[k] - t) <= band, f"missing pair {divmod(k, n)} score {rmap[k]} (t={t})"
     for k in gpu_only.tolist():
         a, b = divmod(k, n)
-        sc = row_dot64(csr, a, b) if csr is not None else s[np.searchsorted(keys, k)]
-        assert abs(sc - t) <= band, f"extra pair {(a, b)} score {sc} (t={t})"
+        sc = dense_dot64(dense, a, b) if dense is not None else row_dot64(csr, a, b, queries)
+        assert abs(sc - t) <= band, f"extra pair {(a, b)} float64 score {sc} (t={t})"
     common = np.intersect1d(keys, rk, assume_unique=True)
     gi = np.searchsorted(keys, common)
     ri = np.searchsorted(rk, common)

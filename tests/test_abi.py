@@ -105,3 +105,26 @@ def test_variant_table_matches_header():
             for k, v in A.VARIANTS.items()}
     assert got == want
     assert len(got) == 9
+
+
+def test_noalloc_binding_rejects_host_and_mistyped_outputs():
+    """The allocation-free join's outputs are written by kernels: the binding refuses a
+    NumPy array, a CPU tensor, a wrong dtype and a strided view before calling the library
+    (no GPU needed; the checks run first)."""
+    import numpy as np
+    import torch
+
+    import paper_1402_3010_gb300 as aps
+
+    i32 = np.zeros(8, np.int32)
+    f32 = np.zeros(8, np.float32)
+    with pytest.raises(ValueError):
+        aps.aps_all_pairs_noalloc(0, i32, i32, f32)
+    ti = torch.zeros(8, dtype=torch.int32)
+    tf = torch.zeros(8, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        aps.aps_all_pairs_noalloc(0, ti, ti, tf)
+    if torch.cuda.is_available():  # pragma: no cover - CPU suite
+        di = torch.zeros(8, dtype=torch.int16, device="cuda")
+        with pytest.raises(ValueError):
+            aps.aps_all_pairs_noalloc(0, di, di, di)

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synth
-from parity import compare
+from parity import compare, dense_dot64
 
 pytestmark = pytest.mark.gpu
 
@@ -46,7 +46,7 @@ def test_dense_mixture_full_parity(aps, n, d, k):
     t = 0.8
     i, j, s, st = run_dense(aps, X, t)
     ref = oracle.dense_all_pairs(X, f32(t))
-    r = compare(i, j, s, ref, f32(t), n)
+    r = compare(i, j, s, ref, f32(t), n, dense=X)
     assert r["pairs"] > 0
     assert st["pairs"] == len(i) and st["candidates"] >= st["pairs"]
 
@@ -61,7 +61,7 @@ def test_dense_many_pairs_near_the_threshold(aps):
     t = 0.3
     i, j, s, st = run_dense(aps, X, t)
     ref = oracle.dense_all_pairs(X, f32(t))
-    compare(i, j, s, ref, f32(t), X.shape[0])
+    compare(i, j, s, ref, f32(t), X.shape[0], dense=X)
     # some reference scores lie just above t: any miss there would fail compare()
     assert np.sum((ref.s >= t) & (ref.s < t + 0.004)) > 10
 
@@ -73,9 +73,9 @@ def test_dense_host_input_and_normalize(aps):
     t = 0.85
     ref = oracle.dense_all_pairs(X, f32(t))
     a = run_dense(aps, X, t, device=False)
-    compare(a[0], a[1], a[2], ref, f32(t), 900)
+    compare(a[0], a[1], a[2], ref, f32(t), 900, dense=X)
     b = run_dense(aps, (X * 2.5).astype(np.float32), t, flags=A.NORMALIZE)
-    compare(b[0], b[1], b[2], ref, f32(t), 900, tol=2e-5)
+    compare(b[0], b[1], b[2], ref, f32(t), 900, tol=2e-5, dense=X)
     with pytest.raises(A.APSError) as e:
         run_dense(aps, (X * 2.5).astype(np.float32), t)
     assert e.value.status == A.EINVAL
@@ -115,8 +115,9 @@ def test_dense_full_size_sampled_rows(aps):
     for k in np.setdiff1d(rk, gk).tolist():
         assert abs(rmap[k] - t) <= 1e-5
     smap = dict(zip(keys[sel].tolist(), s[sel].tolist()))
-    for k in np.setdiff1d(gk, rk).tolist():
-        assert abs(smap[k] - t) <= 1e-5
+    for k in np.setdiff1d(gk, rk).tolist():  # an extra pair is judged by its float64 score
+        a, b = divmod(k, X.shape[0])
+        assert abs(dense_dot64(X, a, b) - t) <= 1e-5
     common = np.intersect1d(gk, rk)
     err = max(abs(smap[k] - rmap[k]) for k in common.tolist())
     assert err <= 1e-5
@@ -138,7 +139,7 @@ def test_dense_misaligned_device_rows(aps):
         i, j, s = aps.pairs_to_numpy(p)
     finally:
         aps.aps_pairs_free(p)
-    compare(i, j, s, oracle.dense_all_pairs(X, f32(t)), f32(t), 1000)
+    compare(i, j, s, oracle.dense_all_pairs(X, f32(t)), f32(t), 1000, dense=X)
 
 
 
@@ -170,4 +171,4 @@ def test_dense_wait_limit_expires_and_context_stays_usable(aps, n, d, wait_ns):
         assert np.array_equal(a, b)
     if n <= 2000:
         ref = oracle.dense_all_pairs(X, f32(t))
-        assert compare(after[0], after[1], after[2], ref, f32(t), n)["pairs"] > 0
+        assert compare(after[0], after[1], after[2], ref, f32(t), n, dense=X)["pairs"] > 0

@@ -68,7 +68,7 @@ def test_query_parity(aps, n, t_build, t_query):
     finally:
         A.aps_index_free(h)
     ref = oracle.bruteforce_cross(q, c, f32(t_query))
-    r = compare(i, j, s, ref, f32(t_query), c.n, self_join=False)
+    r = compare(i, j, s, ref, f32(t_query), c.n, self_join=False, csr=c, queries=q)
     assert r["pairs"] > 0
 
 
@@ -150,7 +150,7 @@ def test_serving_results_alone_equal_results_in_the_mix(aps):
     I = np.concatenate([x[0] + a for (a, _), x in zip(bounds, mixed)])
     J = np.concatenate([x[1] for x in mixed])
     S = np.concatenate([x[2] for x in mixed])
-    compare(I, J, S, oracle.bruteforce_cross(q, c, f32(t)), f32(t), c.n, self_join=False)
+    compare(I, J, S, oracle.bruteforce_cross(q, c, f32(t)), f32(t), c.n, self_join=False, csr=c, queries=q)
 
 
 def test_serving_cancel_budget_and_errors(aps):
@@ -208,5 +208,5 @@ def test_serving_shape_index_sampled_queries(aps):
     finally:
         A.aps_index_free(h)
     ref = oracle.bruteforce_cross(q, c, f32(t))
-    r = compare(i, j, s, ref, f32(t), c.n, self_join=False)
+    r = compare(i, j, s, ref, f32(t), c.n, self_join=False, csr=c, queries=q)
     assert r["pairs"] > 0

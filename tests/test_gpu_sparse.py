@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synth
-from parity import compare
+from parity import compare, row_dot64
 
 pytestmark = pytest.mark.gpu
 
@@ -453,8 +453,8 @@ def test_full_size_200k_sampled_rows(aps, t):
     assert len(rmap) > 0
     for k in set(rmap) - set(gmap):  # only pairs inside the 1e-5 band may differ
         assert abs(rmap[k] - t) <= 1e-5
-    for k in set(gmap) - set(rmap):
-        assert abs(gmap[k] - t) <= 1e-5
+    for k in set(gmap) - set(rmap):  # an extra pair is judged by its float64 score
+        assert abs(row_dot64(c, *divmod(k, c.n)) - t) <= 1e-5
     common = set(gmap) & set(rmap)
     assert max(abs(gmap[k] - rmap[k]) for k in common) <= 1e-5
 

@@ -196,6 +196,6 @@ def test_every_query_tile_shape_matches_the_oracle(A):
                     A.aps_pairs_free(p)
             finally:
                 A.aps_index_free(h)
-            compare(i, j, s, ref, t, c.n, self_join=False)
+            compare(i, j, s, ref, t, c.n, self_join=False, csr=c, queries=q)
     finally:
         A.aps_set_tuning(A.aps_tuning_default(), default_q)

@@ -8,6 +8,7 @@ so that a run stopping at the first failure has already run every other test."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from parity import compare
 
@@ -60,7 +61,60 @@ def test_noalloc_matches_allocating_join_on_two_calls(aps, case):
             assert np.abs(gs.astype(np.float64) - rs).max(initial=0.0) <= 1e-5
             keys = gi.astype(np.int64) * c.n + gj
             assert np.all(np.diff(keys) > 0)
+            # and the definition itself: the float64 brute force of the oracle
+            compare(gi, gj, gs, oracle.bruteforce(c, float(np.float32(t))), float(np.float32(t)), c.n, csr=c)
+            st = aps.aps_index_stats(h)
+            assert st["pairs"] == n and st["candidates"] >= n
             s.zero_()
+    finally:
+        aps.aps_index_free(h)
+
+
+def test_noalloc_allocates_nothing(aps):
+    """With the library's allocation-failure hook armed, the allocation-free join still
+    succeeds, and the hook is still armed afterwards: the next allocating join fails."""
+    import torch
+
+    c, t = synth.config_small(seed=1)
+    h = aps.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, t)
+    try:
+        ri, rj, _ = _ref(aps, h)
+        out = [torch.empty(len(ri) + 8, dtype=dt, device="cuda") for dt in (torch.int32, torch.int32, torch.float32)]
+        aps.aps_debug_fail_alloc(1)
+        try:
+            n = aps.aps_all_pairs_noalloc(h, *out)
+            assert n == len(ri)
+            assert np.array_equal(out[0][:n].cpu().numpy(), ri) and np.array_equal(out[1][:n].cpu().numpy(), rj)
+            with pytest.raises(aps.APSError) as e:
+                p = aps.aps_all_pairs(h)
+                aps.aps_pairs_free(p)
+            assert e.value.status == aps.ENOMEM
+        finally:
+            aps.aps_debug_fail_alloc(0)
+        p = aps.aps_all_pairs(h)  # disarmed: allocations work again
+        assert int(p.count) == len(ri)
+        aps.aps_pairs_free(p)
+    finally:
+        aps.aps_index_free(h)
+
+
+def test_noalloc_rejects_host_output_arrays_in_the_library(aps):
+    """The C entry point itself refuses host memory for its output arrays (callers of the C
+    ABI bypass the binding's checks)."""
+    import ctypes
+
+    import torch
+
+    c, t = synth.config_small(seed=1)
+    h = aps.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, t)
+    try:
+        host = np.zeros(64, np.int32)
+        dev = torch.empty(64, dtype=torch.int32, device="cuda")
+        cnt = ctypes.c_int64(0)
+        lib = aps.load()
+        st = lib.aps_all_pairs_noalloc(h, host.ctypes.data, dev.data_ptr(), dev.data_ptr(), 64, ctypes.byref(cnt),
+                                       None)
+        assert st == aps.EINVAL and "device memory" in aps.aps_last_error()
     finally:
         aps.aps_index_free(h)
 
