@@ -251,13 +251,16 @@ __global__ void k_lptr(const uint64_t *__restrict__ keys, int64_t nsuf, int64_t 
 // Interleaved rows and per-vector metadata read by the join.
 __global__ void k_pack(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
                        const float *__restrict__ cval, const int32_t *__restrict__ len,
-                       const int32_t *__restrict__ split, const float *__restrict__ mwpre, int64_t N, int64_t nnz,
-                       int2 *crow, int4 *vmeta) {
+                       const int32_t *__restrict__ split, const float *__restrict__ mwpre,
+                       const float *__restrict__ pnorm, int64_t N, int64_t nnz, int2 *crow, int4 *vmeta,
+                       int4 *vcand) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += stride)
         crow[p] = make_int2(crank[p], __float_as_int(cval[p]));
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += stride)
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += stride) {
         vmeta[x] = make_int4((int32_t)cptr[x], len[x], split[x], __float_as_int(mwpre[x]));
+        vcand[x] = make_int4((int32_t)cptr[x], split[x], __float_as_int(mwpre[x]), __float_as_int(pnorm[x]));
+    }
 }
 
 // Window offsets inside each list of a multi-window instance: w[i] = the offset in list R
@@ -518,8 +521,10 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
         }
         APS_TRY(d.crow.alloc((size_t)std::max<int64_t>(nnz, 1), s));
         APS_TRY(d.vmeta.alloc((size_t)std::max<int64_t>(N, 1), s));
+        APS_TRY(d.vcand.alloc((size_t)std::max<int64_t>(N, 1), s));
         k_pack<<<grid_for(std::max(nnz, N), T256), T256, 0, s>>>(d.cptr.p, d.crank.p, d.cval.p, d.len.p, d.split.p,
-                                                                 d.mwpre.p, N, nnz, d.crow.p, d.vmeta.p);
+                                                                 d.mwpre.p, d.pnorm.p, N, nnz, d.crow.p, d.vmeta.p,
+                                                                 d.vcand.p);
         APS_LAUNCH_CHECK();
     }
     // ---- join work list

@@ -11,7 +11,9 @@
 //   crow[nnz]   the same rows interleaved as {int32 rank, float32 value} (8 bytes)
 //   vmeta[N]    {int32 row offset, int32 |x|, int32 |x'|, float32 maxweight(x')} (16 bytes)
 //   pnorm[N]    an upper bound of ||x'||_2 (with the 1e-3 norm tolerance of the queries):
-//               dot(q, x') <= ||x'||_2 for any unit q, a 4-byte first filter before vmeta
+//               dot(q, x') <= ||x'||_2 for any unit q
+//   vcand[N]    what verification reads of a candidate y, in one 16-byte load: {int32 row
+//               offset, int32 |y'|, float32 maxweight(y'), float32 ||y'||_2 bound}
 //   post[]      posting entries {int32 local vector id | min(|y|, 255) << 24, float32
 //               weight} (8 bytes), in increasing id inside each list; the size class in
 //               the top byte lets minsize skip an entry without another load (instances
@@ -34,6 +36,7 @@ constexpr int JOIN_XCAP = 2048;   // x's row kept in shared memory when |x| <= X
 // up to 128 (W/NW = 1280 for every group shape)
 constexpr int JOIN_ECAP = JOIN_WMAX / (JOIN_THREADS / 32) + 128;
 constexpr int JOIN_STAGE_SLAB = 4096;  // staging slots a query group reserves at a time
+constexpr int JOIN_ESM = 64;           // emitted pairs of a window a warp keeps in shared memory
 
 struct InstDesc {
     int64_t vbase;   // first global vector id
@@ -64,6 +67,7 @@ struct IndexArrays {
     DBuf<float> cval;
     DBuf<int2> crow;
     DBuf<int4> vmeta;
+    DBuf<int4> vcand;  // {row offset, |x'|, maxweight(x'), ||x'||_2 bound} per vector
     DBuf<int32_t> len, split, qsplit;
     DBuf<float> mw, mwpre;
     DBuf<float> pnorm;  // ||x'||_2 of the unindexed prefix (rounded up, with the norm tolerance)
@@ -135,7 +139,8 @@ aps_status pairs_to_host(aps_pairs *p, cudaStream_t s);
 // dimension ranks and sorted by rank, with |q|, maxweight(q) and the remscore boundary.
 struct QueryArrays {
     DBuf<int2> crow;     // {rank, value} per component, rows in rank order
-    DBuf<int4> vmeta;    // {row offset, |q|, 0, 0}
+    DBuf<int4> vmeta;
+    DBuf<int4> vcand;  // {row offset, |x'|, maxweight(x'), ||x'||_2 bound} per vector    // {row offset, |q|, 0, 0}
     DBuf<int32_t> qsplit;
     DBuf<float> mw;
     int64_t nq = 0, nnz = 0;

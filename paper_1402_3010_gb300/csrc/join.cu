@@ -10,9 +10,9 @@
 //      first over the components with remscore >= t (these may create candidates), then
 //      over the rest, which only update candidates that exist (remscore); entries with |y|
 //      below minsize are skipped using the size class stored in the entry. A holds 32-bit
-//      fixed-point sums (products rounded to multiples of 2^-30, a creating product at
-//      least one unit), so its updates are native integer shared-memory atomics and a
-//      slot is a candidate exactly when it is non-zero. Lists are in id order, so a
+//      fixed-point sums (products rounded up to multiples of 2^-30, so a creating product
+//      is at least one unit), so its updates are native integer shared-memory atomics and
+//      a slot is a candidate exactly when it is non-zero. Lists are in id order, so a
 //      warp's 32 lanes add into 32 increasing slots;
 //   2. verify: each warp scans its share of A 32 slots at a time (a ballot of the
 //      non-zero slots is one 32-bit word of candidates) and takes the candidates in slot
@@ -50,7 +50,7 @@ struct JoinParams {
     int64_t cls_begin[5];
     const int2 *crow;    // rank-ordered rows {rank, value}
     const int4 *vmeta;   // {row offset, |x|, |x'|, maxweight(x')}
-    const float *pnorm;  // ||y'||_2 upper bound
+    const int4 *vcand;   // {row offset, |y'|, maxweight(y'), ||y'||_2 bound}
     const int32_t *qsplit;
     const float *mw;
     const int64_t *lptr;
@@ -86,6 +86,7 @@ __host__ __device__ constexpr int group_bytes(int G) {
            + 4 * (JOIN_THREADS / G)                  // c_xv
            + 4 * (JOIN_RMAX / G)                     // xtab
            + 8 * (JOIN_XCAP / G)                     // x's row
+           + 8 * JOIN_ESM * (JOIN_THREADS / G / 32)  // the warps' emitted pairs of a window
            + 8 * 32                                  // wsum
            + 4 * 32                                  // wcnt
            + 8 * 8;                                  // broadcast and the staging slab
@@ -147,19 +148,60 @@ __device__ __forceinline__ float x_at(int r, const float *xtab, int RG, const in
     return (lo < xs && xr[lo].x == r) ? __int_as_float(xr[lo].y) : 0.f;
 }
 
-// dot(x, y') over the |y'| leading (unindexed) entries of y's rank-ordered row.
+// The accumulation of one warp over chunks [ch, che) of the current component batch
+// (Alg. 2's A[y] += x[i] * y[i]). Chunk ch of component cc covers entries
+// (ch - c_ch0[cc]) * 128 .. + 127 of that component's segment, and no further than its end.
+// Each product is rounded up to a multiple of 2^-30 (so a creating product is at least one
+// unit and its slot becomes non-zero); CREATE: the component may create candidates,
+// otherwise it only adds where A is already non-zero (remscore). FIRST: the window holds
+// ids at or below x's (slots below lo are skipped).
+template <bool CREATE, bool FIRST>
+__device__ __forceinline__ void walk_chunks(int ch, const int che, int cc, const int64_t *c_start,
+                                            const int32_t *c_cnt, const int32_t *c_ch0, const float *c_xv,
+                                            const int2 *__restrict__ post, uint32_t *A, const uint32_t smin_tag,
+                                            const int32_t idmask, const int w0, const int lo, const int lane) {
+    const int2 *seg = post + c_start[cc];
+    int cnt = c_cnt[cc], cch0 = c_ch0[cc], cnext = c_ch0[cc + 1];
+    float cxv = c_xv[cc] * 1073741824.f;  // x's value scaled by 2^30 (exact)
+    for (; ch < che; ch++) {
+        if (ch >= cnext) {
+            cc++;
+            seg = post + c_start[cc];
+            cnt = c_cnt[cc];
+            cch0 = cnext;
+            cnext = c_ch0[cc + 1];
+            cxv = c_xv[cc] * 1073741824.f;
+        }
+        const int off = ((ch - cch0) << 7) + lane;
+        const int rem = cnt - off;  // entries from this lane's first one to the segment's end
+        const int2 *pp = seg + off;
+        int2 ent[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) ent[u] = u * 32 < rem ? __ldg(pp + u * 32) : make_int2(0, 0);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (u * 32 >= rem || (uint32_t)ent[u].x < smin_tag) continue;  // past the end; minsize
+            const int slot = (ent[u].x & idmask) - w0;
+            if (FIRST && slot < lo) continue;
+            const uint32_t q = __float2uint_ru(cxv * __int_as_float(ent[u].y));
+            if (CREATE || A[slot] != 0u) atomicAdd(&A[slot], q);
+        }
+    }
+}
+
+// dot(x, y') over the |y'| leading (unindexed) entries of y's rank-ordered row, by one
+// lane (short prefixes): two entries per step.
 __device__ __forceinline__ float dot_prefix(const int2 *__restrict__ yr, int ys, const float *xtab, int RG,
-                                           const int2 *xr, int xs, const int2 *__restrict__ xrow,
-                                           int xl) {
+                                           const int2 *xr, int xs, const int2 *__restrict__ xrow, int xl) {
     float acc = 0.f;
     int k = 0;
     for (; k + 2 <= ys; k += 2) {
-        const int2 e0 = yr[k], e1 = yr[k + 1];
+        const int2 e0 = __ldg(yr + k), e1 = __ldg(yr + k + 1);
         acc = fmaf(x_at(e0.x, xtab, RG, xr, xs, xrow, xl), __int_as_float(e0.y), acc);
         acc = fmaf(x_at(e1.x, xtab, RG, xr, xs, xrow, xl), __int_as_float(e1.y), acc);
     }
     if (k < ys) {
-        const int2 e0 = yr[k];
+        const int2 e0 = __ldg(yr + k);
         acc = fmaf(x_at(e0.x, xtab, RG, xr, xs, xrow, xl), __int_as_float(e0.y), acc);
     }
     return acc;
@@ -194,7 +236,8 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     float *xtab = c_xv + GT;                                        // [RG]
     int2 *xr = reinterpret_cast<int2 *>(xtab + RG);
     const int XG = JOIN_XCAP / G;
-    int64_t *wsum = reinterpret_cast<int64_t *>(xr + XG);
+    int2 *es = reinterpret_cast<int2 *>(xr + XG) + gw * JOIN_ESM;  // this warp's emitted pairs
+    int64_t *wsum = reinterpret_cast<int64_t *>(xr + XG + NW * JOIN_ESM);
     int32_t *wcnt = reinterpret_cast<int32_t *>(wsum + 32);
     int64_t *bc = reinterpret_cast<int64_t *>(wcnt + 32);
     int2 *elist = P.scratch + ((size_t)blockIdx.x * NWARPS + (threadIdx.x >> 5)) * JOIN_ECAP;
@@ -320,38 +363,14 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                         }
                         cc = a;
                     }
-                    // x's value scaled by 2^30 (exact): products convert straight to A's units
-                    int64_t cst = c_start[cc], cen = cst + c_cnt[cc];
-                    int cch0 = c_ch0[cc];
-                    float cxv = c_xv[cc] * 1073741824.f;
-                    for (; ch < che; ch++) {
-                        if (ch >= c_ch0[cc + 1]) {
-                            cc++;
-                            cst = c_start[cc];
-                            cen = cst + c_cnt[cc];
-                            cch0 = c_ch0[cc];
-                            cxv = c_xv[cc] * 1073741824.f;
-                        }
-                        const int64_t e0 = cst + (int64_t)(ch - cch0) * 128 + lane;
-                        int2 ent[4];
-#pragma unroll
-                        for (int u = 0; u < 4; u++)
-                            ent[u] = (e0 + u * 32 < cen) ? __ldg(&P.post[e0 + u * 32]) : make_int2(0, 0);
-#pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            if (e0 + u * 32 >= cen) continue;
-                            if ((uint32_t)ent[u].x < smin_tag) continue;  // minsize
-                            const int slot = (ent[u].x & idmask) - w0;
-                            if (slot < lo) continue;
-                            // x[i] * y[i] in units of 2^-30, rounded to nearest; a creating
-                            // product is at least one unit so that its slot becomes non-zero
-                            const uint32_t q = __float2uint_rn(__fmul_rn(cxv, __int_as_float(ent[u].y)));
-                            if (phase == 0) {
-                                atomicAdd(&A[slot], q + (q == 0u));
-                            } else if (A[slot] != 0u) {
-                                atomicAdd(&A[slot], q);
-                            }
-                        }
+                    // four specialisations: creating or updating, first window (ids at or
+                    // below x present) or not
+                    if (phase == 0) {
+                        if (lo > 0) walk_chunks<true, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, smin_tag, idmask, w0, lo, lane);
+                        else walk_chunks<true, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, smin_tag, idmask, w0, lo, lane);
+                    } else {
+                        if (lo > 0) walk_chunks<false, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, smin_tag, idmask, w0, lo, lane);
+                        else walk_chunks<false, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, smin_tag, idmask, w0, lo, lane);
                     }
                 }
                 gsync(G, g, GT);
@@ -368,11 +387,19 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
             const int wb = wlo + gw * wper, we = min(wb + wper, whi);
             int ne = 0;
             for (int wq = wb; wq < we; wq += 32) {
+                // word k of these 32 = the ballot of the non-zero slots among (wq + k) * 32 +
+                // 0..31, kept by lane k; the A loads are issued eight at a time
                 uint32_t word = 0u;
                 const int nwd = min(32, we - wq);
-                for (int k = 0; k < nwd; k++) {
-                    const uint32_t b = __ballot_sync(0xffffffffu, A[((wq + k) << 5) + lane] != 0u);
-                    if (lane == k) word = b;
+                for (int k0 = 0; k0 < nwd; k0 += 8) {
+                    uint32_t a8[8];
+#pragma unroll
+                    for (int k = 0; k < 8; k++) a8[k] = k0 + k < nwd ? A[((wq + k0 + k) << 5) + lane] : 0u;
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        const uint32_t b = __ballot_sync(0xffffffffu, a8[k] != 0u);
+                        if (lane == k0 + k) word = b;
+                    }
                 }
                 const int c = __popc(word);
                 int T;
@@ -391,40 +418,42 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     bool emit = false;
                     float sc = 0.f, v = 0.f;
                     int s = 0;
-                    int4 ym = make_int4(0, 0, 0, 0);
-                    // 0: rejected, 1: score known, 2: short dot(x, y') left, 3: long dot left
+                    int4 yc = make_int4(0, 0, 0, 0);  // {row offset, |y'|, maxweight(y'), ||y'||_2 bound}
+                    // 0: rejected or emitted, 1: score known, 2: short dot(x, y') left, 3: long one
                     int stage = 0;
                     if (have) {
                         for (int k = p - oex; k > 0; k--) ow &= ow - 1u;
                         s = ((wq + own) << 5) + (__ffs(ow) - 1);
                         v = __uint2float_rn(A[s]) * 9.31322574615478515625e-10f;  // 2^-30
                         A[s] = 0u;
-                        const int64_t gy = I.vbase + w0 + s;
-                        sc = v;
-                        // dot(x, y') <= ||y'||_2: most candidates stop here, on a 4-byte load
-                        // (a bound on the prefix dot like upperbound; both off with NO_UPPERBOUND)
-                        if (!f_upper || v + __ldg(&P.pnorm[gy]) > t - beta) {
-                            ym = __ldg(&P.vmeta[gy]);
-                            const int ys = ym.z;
-                            bool ok = true;
-                            if (ys > 0 && f_upper)
-                                ok = v + (float)min(ys, xl) * mwx * __int_as_float(ym.w) >= t - beta;
-                            if (ok) stage = ys == 0 ? 1 : (ys <= 16 ? 2 : 3);
+                        yc = __ldg(&P.vcand[I.vbase + w0 + s]);
+                        const int ys = yc.y;
+                        bool ok = true;
+                        if (f_upper) {
+                            // dot(x, y') <= ||y'||_2 (Cauchy-Schwarz; most candidates stop here),
+                            // then the paper's upperbound; both off with NO_UPPERBOUND
+                            ok = v + __int_as_float(yc.w) > t - beta;
+                            if (ok && ys > 0) ok = v + (float)min(ys, xl) * mwx * __int_as_float(yc.z) >= t - beta;
+                        }
+                        if (ok) {
+                            sc = v;
+                            stage = ys == 0 ? 1 : (ys <= 16 ? 2 : 3);
                         }
                     }
-                    if (stage == 2) {
+                    if (stage == 2) {  // short prefixes: each lane its own candidate
                         n_verified++;
-                        sc = v + dot_prefix(P.crow + ym.x, ym.z, xtab, RG, xr, xs, xrow, xl);
+                        sc = v + dot_prefix(P.crow + yc.x, yc.y, xtab, RG, xr, xs, xrow, xl);
                         stage = 1;
                     }
-                    // long prefixes: the whole warp computes one dot(x, y') at a time
+                    // long prefixes: the whole warp takes one candidate at a time, its lanes
+                    // reading y's prefix entries side by side
                     for (unsigned lm = __ballot_sync(0xffffffffu, stage == 3); lm; lm &= lm - 1u) {
                         const int src = __ffs(lm) - 1;
-                        const int yo = __shfl_sync(0xffffffffu, ym.x, src);
-                        const int yl = __shfl_sync(0xffffffffu, ym.z, src);
+                        const int yo = __shfl_sync(0xffffffffu, yc.x, src);
+                        const int yl = __shfl_sync(0xffffffffu, yc.y, src);
                         float acc = 0.f;
                         for (int k = lane; k < yl; k += 32) {
-                            const int2 e = P.crow[yo + k];
+                            const int2 e = __ldg(&P.crow[yo + k]);
                             acc = fmaf(x_at(e.x, xtab, RG, xr, xs, xrow, xl), __int_as_float(e.y), acc);
                         }
 #pragma unroll
@@ -445,10 +474,12 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     }
                     // inside the band: float64 dot(x, y) over all of y, one candidate at a
                     // time across the warp (x's values from shared memory, exact products)
+                    int yfull = 0;
+                    if (stage == 1) yfull = __ldg(&P.vmeta[I.vbase + w0 + s]).y;
                     for (unsigned lm = __ballot_sync(0xffffffffu, stage == 1); lm; lm &= lm - 1u) {
                         const int src = __ffs(lm) - 1;
-                        const int yo = __shfl_sync(0xffffffffu, ym.x, src);
-                        const int yl = __shfl_sync(0xffffffffu, ym.y, src);
+                        const int yo = __shfl_sync(0xffffffffu, yc.x, src);
+                        const int yl = __shfl_sync(0xffffffffu, yfull, src);
                         double acc = 0.0;
                         for (int k = lane; k < yl; k += 32) {
                             const int2 e = P.crow[yo + k];
@@ -463,7 +494,11 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                         }
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, emit);
-                    if (emit) elist[ne + __popc(bal & lt_mask)] = make_int2(w0 + s, __float_as_int(sc));
+                    if (emit) {  // the warp's first JOIN_ESM pairs of the window stay in shared memory
+                        const int pos = ne + __popc(bal & lt_mask);
+                        const int2 pr = make_int2(w0 + s, __float_as_int(sc));
+                        if (pos < JOIN_ESM) es[pos] = pr; else elist[pos] = pr;
+                    }
                     ne += __popc(bal);
                     n_cand += have ? 1ull : 0ull;
                 }
@@ -506,7 +541,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
             // ---------------- copy the warp's emitted pairs to the reserved run
             if (bc[2] != 0) {
                 int2 *dst = P.stage + bc[1] + wcnt[gw];
-                for (int k = lane; k < ne; k += 32) dst[k] = elist[k];
+                for (int k = lane; k < ne; k += 32) dst[k] = k < JOIN_ESM ? es[k] : elist[k];
             }
             __syncwarp();
         }
@@ -703,7 +738,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
             const int grid = set_classes(P, ix, sms, &smem);
             P.crow = d.crow.p;
             P.vmeta = d.vmeta.p;
-            P.pnorm = d.pnorm.p;
+            P.vcand = d.vcand.p;
             P.qsplit = d.qsplit.p;
             P.mw = d.mw.p;
             P.lptr = d.lptr.p;
@@ -937,7 +972,7 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
         const int grid = set_classes(P, ix, grid_max, &smem);
         P.crow = d.crow.p;
         P.vmeta = d.vmeta.p;
-        P.pnorm = d.pnorm.p;
+        P.vcand = d.vcand.p;
         P.qsplit = d.qsplit.p;
         P.mw = d.mw.p;
         P.lptr = d.lptr.p;
@@ -1046,7 +1081,7 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
             P.cls_begin[1] = nitems;
             P.crow = d.crow.p;
             P.vmeta = d.vmeta.p;
-            P.pnorm = d.pnorm.p;
+            P.vcand = d.vcand.p;
             P.qsplit = d.qsplit.p;
             P.mw = d.mw.p;
             P.lptr = d.lptr.p;
