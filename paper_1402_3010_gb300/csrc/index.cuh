@@ -36,7 +36,6 @@ constexpr int JOIN_XCAP = 2048;   // x's row kept in shared memory when |x| <= X
 // up to 128 (W/NW = 1280 for every group shape)
 constexpr int JOIN_ECAP = JOIN_WMAX / (JOIN_THREADS / 32) + 128;
 constexpr int JOIN_STAGE_SLAB = 4096;  // staging slots a query group reserves at a time
-constexpr int JOIN_ESM = 64;           // emitted pairs of a window a warp keeps in shared memory
 
 struct InstDesc {
     int64_t vbase;   // first global vector id

@@ -11,12 +11,13 @@
 //      over the rest, which only update candidates that exist (remscore); entries with |y|
 //      below minsize are skipped using the size class stored in the entry. A holds 32-bit
 //      fixed-point sums (products rounded up to multiples of 2^-30, so a creating product
-//      is at least one unit), so its updates are native integer shared-memory atomics and
-//      a slot is a candidate exactly when it is non-zero. Lists are in id order, so a
-//      warp's 32 lanes add into 32 increasing slots;
-//   2. verify: each warp scans its share of A 32 slots at a time (a ballot of the
-//      non-zero slots is one 32-bit word of candidates) and takes the candidates in slot
-//      order, one per lane: A[y] + ||y'||_2 < t rejects cheaply, then the
+//      is at least one unit), so its updates are native integer shared-memory atomics. A
+//      creating update that finds its slot still zero (a plain read before the add) also
+//      sets the slot's bit in a bitmap of candidates: the first update of a slot always
+//      does, so every candidate is marked, at one bitmap update per candidate rather than
+//      per entry. Lists are in id order, so a warp's 32 lanes add into 32 increasing slots;
+//   2. verify: each warp walks its share of the bitmap and takes the marked slots in slot
+//      order, one candidate per lane: A[y] + ||y'||_2 < t rejects cheaply, then the
 //      upperbound test A[y] + min(|y'|, |x|) * maxweight(x) * maxweight(y') >= t, then
 //      s = A[y] + dot(x, y') with y' the unindexed prefix of y; scores within a band of
 //      t are recomputed in float64 and decided there;
@@ -86,7 +87,7 @@ __host__ __device__ constexpr int group_bytes(int G) {
            + 4 * (JOIN_THREADS / G)                  // c_xv
            + 4 * (JOIN_RMAX / G)                     // xtab
            + 8 * (JOIN_XCAP / G)                     // x's row
-           + 8 * JOIN_ESM * (JOIN_THREADS / G / 32)  // the warps' emitted pairs of a window
+           + 4 * (JOIN_WMAX / G / 32)                // bitmap of the window's candidates
            + 8 * 32                                  // wsum
            + 4 * 32                                  // wcnt
            + 8 * 8;                                  // broadcast and the staging slab
@@ -152,13 +153,16 @@ __device__ __forceinline__ float x_at(int r, const float *xtab, int RG, const in
 // (Alg. 2's A[y] += x[i] * y[i]). Chunk ch of component cc covers entries
 // (ch - c_ch0[cc]) * 128 .. + 127 of that component's segment, and no further than its end.
 // Each product is rounded up to a multiple of 2^-30 (so a creating product is at least one
-// unit and its slot becomes non-zero); CREATE: the component may create candidates,
-// otherwise it only adds where A is already non-zero (remscore). FIRST: the window holds
-// ids at or below x's (slots below lo are skipped).
+// unit and its slot becomes non-zero); CREATE: the component may create candidates, and an
+// add that found its slot zero marks the slot in bm (the first add to a slot always finds
+// it zero, so every candidate is marked; a few concurrent first adds mark it again, which
+// is harmless); otherwise it only adds where A is already non-zero (remscore). FIRST: the
+// window holds ids at or below x's (slots below lo are skipped).
 template <bool CREATE, bool FIRST>
 __device__ __forceinline__ void walk_chunks(int ch, const int che, int cc, const int64_t *c_start,
                                             const int32_t *c_cnt, const int32_t *c_ch0, const float *c_xv,
-                                            const int2 *__restrict__ post, uint32_t *A, const uint32_t smin_tag,
+                                            const int2 *__restrict__ post, uint32_t *A, uint32_t *bm,
+                                            const uint32_t smin_tag,
                                             const int32_t idmask, const int w0, const int lo, const int lane) {
     const int2 *seg = post + c_start[cc];
     int cnt = c_cnt[cc], cch0 = c_ch0[cc], cnext = c_ch0[cc + 1];
@@ -184,7 +188,13 @@ __device__ __forceinline__ void walk_chunks(int ch, const int che, int cc, const
             const int slot = (ent[u].x & idmask) - w0;
             if (FIRST && slot < lo) continue;
             const uint32_t q = __float2uint_ru(cxv * __int_as_float(ent[u].y));
-            if (CREATE || A[slot] != 0u) atomicAdd(&A[slot], q);
+            const uint32_t old = A[slot];
+            if (CREATE) {
+                atomicAdd(&A[slot], q);
+                if (old == 0u) atomicOr(&bm[slot >> 5], 1u << (slot & 31));
+            } else if (old != 0u) {
+                atomicAdd(&A[slot], q);
+            }
         }
     }
 }
@@ -236,14 +246,15 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     float *xtab = c_xv + GT;                                        // [RG]
     int2 *xr = reinterpret_cast<int2 *>(xtab + RG);
     const int XG = JOIN_XCAP / G;
-    int2 *es = reinterpret_cast<int2 *>(xr + XG) + gw * JOIN_ESM;  // this warp's emitted pairs
-    int64_t *wsum = reinterpret_cast<int64_t *>(xr + XG + NW * JOIN_ESM);
+    uint32_t *bm = reinterpret_cast<uint32_t *>(xr + XG);            // [WG / 32]
+    int64_t *wsum = reinterpret_cast<int64_t *>(bm + WG / 32);
     int32_t *wcnt = reinterpret_cast<int32_t *>(wsum + 32);
     int64_t *bc = reinterpret_cast<int64_t *>(wcnt + 32);
     int2 *elist = P.scratch + ((size_t)blockIdx.x * NWARPS + (threadIdx.x >> 5)) * JOIN_ECAP;
     const unsigned lt_mask = (1u << lane) - 1u;
 
     for (int i = gt; i < WG; i += GT) A[i] = 0u;
+    for (int i = gt; i < WG / 32; i += GT) bm[i] = 0u;
     if (gt == 0) bc[3] = bc[4] = bc[5] = 0;  // this group's staging slab: base, used, size
 
     for (;;) {
@@ -366,40 +377,31 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     // four specialisations: creating or updating, first window (ids at or
                     // below x present) or not
                     if (phase == 0) {
-                        if (lo > 0) walk_chunks<true, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, smin_tag, idmask, w0, lo, lane);
-                        else walk_chunks<true, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, smin_tag, idmask, w0, lo, lane);
+                        if (lo > 0) walk_chunks<true, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
+                        else walk_chunks<true, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
                     } else {
-                        if (lo > 0) walk_chunks<false, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, smin_tag, idmask, w0, lo, lane);
-                        else walk_chunks<false, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, smin_tag, idmask, w0, lo, lane);
+                        if (lo > 0) walk_chunks<false, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
+                        else walk_chunks<false, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
                     }
                 }
                 gsync(G, g, GT);
             }
             if (!created) continue;  // no candidate can exist in this window
-            // ---------------- verify. A slot is a candidate when A is non-zero. Each warp
-            // scans its share of A 1024 slots at a time: word k of the 32 (a ballot of the
-            // non-zero slots among 32) goes to lane k. The set bits are taken in slot order,
-            // 32 candidates per batch: lane j of a batch takes the candidate at position
-            // b + j, located from the lanes' popcount prefix. Taken slots are cleared in A,
-            // and the emitted (y, score) go to the warp's scratch list in increasing y.
+            // ---------------- verify. The creating pass marked every candidate in bm. Each
+            // warp walks its share of bm 32 words (1024 slots) at a time and takes the set
+            // bits in slot order, 32 candidates per batch: lane j of a batch takes the
+            // candidate at position b + j, located from the lanes' popcount prefix. Taken
+            // slots are cleared in A (bm words as they are read), and the emitted (y, score)
+            // go to the warp's scratch list in increasing y.
             const int wlo = lo >> 5, whi = (wn + 31) >> 5;
             const int wper = (whi - wlo + NW - 1) / NW;
             const int wb = wlo + gw * wper, we = min(wb + wper, whi);
             int ne = 0;
             for (int wq = wb; wq < we; wq += 32) {
-                // word k of these 32 = the ballot of the non-zero slots among (wq + k) * 32 +
-                // 0..31, kept by lane k; the A loads are issued eight at a time
                 uint32_t word = 0u;
-                const int nwd = min(32, we - wq);
-                for (int k0 = 0; k0 < nwd; k0 += 8) {
-                    uint32_t a8[8];
-#pragma unroll
-                    for (int k = 0; k < 8; k++) a8[k] = k0 + k < nwd ? A[((wq + k0 + k) << 5) + lane] : 0u;
-#pragma unroll
-                    for (int k = 0; k < 8; k++) {
-                        const uint32_t b = __ballot_sync(0xffffffffu, a8[k] != 0u);
-                        if (lane == k0 + k) word = b;
-                    }
+                if (wq + lane < we) {
+                    word = bm[wq + lane];
+                    bm[wq + lane] = 0u;
                 }
                 const int c = __popc(word);
                 int T;
@@ -494,11 +496,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                         }
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, emit);
-                    if (emit) {  // the warp's first JOIN_ESM pairs of the window stay in shared memory
-                        const int pos = ne + __popc(bal & lt_mask);
-                        const int2 pr = make_int2(w0 + s, __float_as_int(sc));
-                        if (pos < JOIN_ESM) es[pos] = pr; else elist[pos] = pr;
-                    }
+                    if (emit) elist[ne + __popc(bal & lt_mask)] = make_int2(w0 + s, __float_as_int(sc));
                     ne += __popc(bal);
                     n_cand += have ? 1ull : 0ull;
                 }
@@ -541,7 +539,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
             // ---------------- copy the warp's emitted pairs to the reserved run
             if (bc[2] != 0) {
                 int2 *dst = P.stage + bc[1] + wcnt[gw];
-                for (int k = lane; k < ne; k += 32) dst[k] = k < JOIN_ESM ? es[k] : elist[k];
+                for (int k = lane; k < ne; k += 32) dst[k] = elist[k];
             }
             __syncwarp();
         }
