@@ -158,12 +158,49 @@ __device__ __forceinline__ float x_at(int r, const float *xtab, int RG, const in
 // it zero, so every candidate is marked; a few concurrent first adds mark it again, which
 // is harmless); otherwise it only adds where A is already non-zero (remscore). FIRST: the
 // window holds ids at or below x's (slots below lo are skipped).
+// One 128-entry chunk of a segment: entries off .. off + 127 of seg[0, cnt), lane l taking
+// off + l, off + l + 32, ... (see walk_chunks).
+template <bool CREATE, bool FIRST>
+__device__ __forceinline__ void walk_chunk(const int2 *__restrict__ seg, const int cnt, const int off, const float cxv,
+                                           uint32_t *A, uint32_t *bm, const uint32_t smin_tag, const int32_t idmask,
+                                           const int w0, const int lo, const int lane) {
+    const int rem = cnt - off - lane;  // entries from this lane's first one to the segment's end
+    const int2 *pp = seg + off + lane;
+    int2 ent[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) ent[u] = u * 32 < rem ? __ldg(pp + u * 32) : make_int2(0, 0);
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        if (u * 32 >= rem || (uint32_t)ent[u].x < smin_tag) continue;  // past the end; minsize
+        const int slot = (ent[u].x & idmask) - w0;
+        if (FIRST && slot < lo) continue;
+        const uint32_t q = __float2uint_ru(cxv * __int_as_float(ent[u].y));
+        const uint32_t old = A[slot];
+        if (CREATE) {
+            atomicAdd(&A[slot], q);
+            if (old == 0u) atomicOr(&bm[slot >> 5], 1u << (slot & 31));
+        } else if (old != 0u) {
+            atomicAdd(&A[slot], q);
+        }
+    }
+}
+
+// The accumulation of one warp over chunks [ch, che) of the current component batch
+// (Alg. 2's A[y] += x[i] * y[i]), the components' segments in shared memory. Chunk ch of
+// component cc covers entries (ch - c_ch0[cc]) * 128 .. + 127 of that component's segment,
+// and no further than its end. Each product is rounded up to a multiple of 2^-30 (so a
+// creating product is at least one unit and its slot becomes non-zero); CREATE: the
+// component may create candidates, and an add that found its slot zero marks the slot in bm
+// (the first add to a slot always finds it zero, so every candidate is marked; a few
+// concurrent first adds mark it again, which is harmless); otherwise it only adds where A
+// is already non-zero (remscore). FIRST: the window holds ids at or below x's (slots below
+// lo are skipped).
 template <bool CREATE, bool FIRST>
 __device__ __forceinline__ void walk_chunks(int ch, const int che, int cc, const int64_t *c_start,
                                             const int32_t *c_cnt, const int32_t *c_ch0, const float *c_xv,
                                             const int2 *__restrict__ post, uint32_t *A, uint32_t *bm,
-                                            const uint32_t smin_tag,
-                                            const int32_t idmask, const int w0, const int lo, const int lane) {
+                                            const uint32_t smin_tag, const int32_t idmask, const int w0, const int lo,
+                                            const int lane) {
     const int2 *seg = post + c_start[cc];
     int cnt = c_cnt[cc], cch0 = c_ch0[cc], cnext = c_ch0[cc + 1];
     float cxv = c_xv[cc] * 1073741824.f;  // x's value scaled by 2^30 (exact)
@@ -176,26 +213,29 @@ __device__ __forceinline__ void walk_chunks(int ch, const int che, int cc, const
             cnext = c_ch0[cc + 1];
             cxv = c_xv[cc] * 1073741824.f;
         }
-        const int off = ((ch - cch0) << 7) + lane;
-        const int rem = cnt - off;  // entries from this lane's first one to the segment's end
-        const int2 *pp = seg + off;
-        int2 ent[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) ent[u] = u * 32 < rem ? __ldg(pp + u * 32) : make_int2(0, 0);
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            if (u * 32 >= rem || (uint32_t)ent[u].x < smin_tag) continue;  // past the end; minsize
-            const int slot = (ent[u].x & idmask) - w0;
-            if (FIRST && slot < lo) continue;
-            const uint32_t q = __float2uint_ru(cxv * __int_as_float(ent[u].y));
-            const uint32_t old = A[slot];
-            if (CREATE) {
-                atomicAdd(&A[slot], q);
-                if (old == 0u) atomicOr(&bm[slot >> 5], 1u << (slot & 31));
-            } else if (old != 0u) {
-                atomicAdd(&A[slot], q);
-            }
+        walk_chunk<CREATE, FIRST>(seg, cnt, (ch - cch0) << 7, cxv, A, bm, smin_tag, idmask, w0, lo, lane);
+    }
+}
+
+// The same with the (at most 32) components of a short x held in registers, lane c holding
+// component c: its segment start st, length cnt, first chunk ch0 and x's value xv.
+template <bool CREATE, bool FIRST>
+__device__ __forceinline__ void walk_chunks_r(int ch, const int che, int cc, const int64_t st, const int cnt_l,
+                                              const int ch0_l, const float xv_l, const int2 *__restrict__ post,
+                                              uint32_t *A, uint32_t *bm, const uint32_t smin_tag, const int32_t idmask,
+                                              const int w0, const int lo, const int lane) {
+    const int2 *seg = post + __shfl_sync(0xffffffffu, st, cc);
+    int cnt = __shfl_sync(0xffffffffu, cnt_l, cc), cch0 = __shfl_sync(0xffffffffu, ch0_l, cc);
+    float cxv = __shfl_sync(0xffffffffu, xv_l, cc) * 1073741824.f;
+    for (; ch < che; ch++) {
+        while (ch >= cch0 + ((cnt + 127) >> 7)) {  // the next component with entries
+            cc++;
+            seg = post + __shfl_sync(0xffffffffu, st, cc);
+            cnt = __shfl_sync(0xffffffffu, cnt_l, cc);
+            cch0 = __shfl_sync(0xffffffffu, ch0_l, cc);
+            cxv = __shfl_sync(0xffffffffu, xv_l, cc) * 1073741824.f;
         }
+        walk_chunk<CREATE, FIRST>(seg, cnt, (ch - cch0) << 7, cxv, A, bm, smin_tag, idmask, w0, lo, lane);
     }
 }
 
@@ -310,6 +350,52 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
             bool created = false;  // any entry of a creating component in this window
             // ---------------- accumulate. Components are walked creating-first (those with
             // remscore >= t), so every batch holds its creating part before its updating part.
+            if (xl <= 32) {
+                // a short x: every warp builds the window's segment table itself, lane c
+                // holding component c (no shared table, no barrier)
+                int64_t st = 0;
+                int cnt = 0;
+                float xv = 0.f;
+                if (lane < xl) {
+                    const int c = lane < ncreate ? qs + lane : lane - ncreate;
+                    const int2 e = c < xs ? xr[c] : xrow[c];
+                    const int64_t R = (int64_t)I.rbase + e.x;
+                    xv = __int_as_float(e.y);
+                    int64_t ls = P.lptr[R], le = P.lptr[R + 1];
+                    if (I.nw > 1) {
+                        const int32_t *wp = P.wptr + I.wbase + (int64_t)e.x * (I.nw + 1);
+                        le = ls + wp[w + 1];
+                        ls = ls + wp[w];
+                    }
+                    cnt = (int32_t)(le - ls);
+                    st = ls;
+                    if (gw == 0) n_visits += (unsigned long long)cnt;
+                }
+                const int nch = (cnt + 127) >> 7;
+                int nchk;
+                const int ch0 = warp_excl_scan_int(nch, lane, &nchk);
+                const int P0 = ncreate > 0 ? __shfl_sync(0xffffffffu, ch0 + nch, ncreate - 1) : 0;
+                created = P0 > 0;
+                for (int phase = 0; phase < 2; phase++) {
+                    const int pb = phase == 0 ? 0 : P0, pe = phase == 0 ? P0 : nchk;
+                    if (pe <= pb) continue;
+                    if (phase == 1 && P0 > 0) gsync(G, g, GT);  // creations land before updates
+                    const int K = (pe - pb + NW - 1) / NW;
+                    const int ch = pb + gw * K;
+                    const int che = min(ch + K, pe);
+                    if (ch >= che) continue;
+                    // the last component with entries whose first chunk is at or before ch
+                    const int cc = 31 - __clz(__ballot_sync(0xffffffffu, nch > 0 && ch0 <= ch));
+                    if (phase == 0) {
+                        if (lo > 0) walk_chunks_r<true, true>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
+                        else walk_chunks_r<true, false>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
+                    } else {
+                        if (lo > 0) walk_chunks_r<false, true>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
+                        else walk_chunks_r<false, false>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
+                    }
+                }
+                gsync(G, g, GT);
+            } else
             for (int c0 = 0; c0 < xl; c0 += GT) {
                 const int cp = c0 + gt;
                 int64_t st = 0;
