@@ -252,14 +252,23 @@ __global__ void k_lptr(const uint64_t *__restrict__ keys, int64_t nsuf, int64_t 
 __global__ void k_pack(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
                        const float *__restrict__ cval, const int32_t *__restrict__ len,
                        const int32_t *__restrict__ split, const float *__restrict__ mwpre,
-                       const float *__restrict__ pnorm, int64_t N, int64_t nnz, int2 *crow, int4 *vmeta,
-                       int4 *vcand) {
+                       const float *__restrict__ pnorm, const int32_t *__restrict__ vinst,
+                       const InstDesc *__restrict__ inst, int64_t N, int64_t nnz, int2 *crow, int4 *vmeta,
+                       int4 *vcand, uint32_t *pn4) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += stride)
         crow[p] = make_int2(crank[p], __float_as_int(cval[p]));
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += stride) {
         vmeta[x] = make_int4((int32_t)cptr[x], len[x], split[x], __float_as_int(mwpre[x]));
         vcand[x] = make_int4((int32_t)cptr[x], split[x], __float_as_int(mwpre[x]), __float_as_int(pnorm[x]));
+        // the smallest 4-bit code c with c * PN4_STEP >= ||x'||_2 (the bound stays a bound)
+        const double pn = (double)pnorm[x];
+        int c = (int)ceil(pn / (double)PN4_STEP);
+        if ((double)c * (double)PN4_STEP < pn) c++;
+        c = min(max(c, 0), 15);
+        const InstDesc &I = inst[vinst[x]];
+        const int64_t lx = x - I.vbase;
+        if (c) atomicOr(&pn4[I.pbase + (lx >> 3)], (uint32_t)c << (4 * (lx & 7)));
     }
 }
 
@@ -350,7 +359,7 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     ix->stream = s;
     // ---- host-side layout of instances: ranks, windows, classes
     std::vector<InstDesc> inst = inst_in;
-    int64_t N = 0, M = 0, nqw = 0, nwptr = 0;
+    int64_t N = 0, M = 0, nqw = 0, nwptr = 0, npw = 0;
     int32_t maxm = 1, maxn = 1, maxnw = 1;
     // tile shape per instance: G query groups per CTA from the size-bucket table (its
     // queryable column for indexes built to answer queries)
@@ -366,6 +375,8 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
         I.packed = I.n < (1 << 24) ? 1 : 0;
         I.qwbase = nqw;
         I.wbase = nwptr;
+        I.pbase = npw;
+        npw += 4 * (((int64_t)I.n + 31) / 32);  // 32 codes per 16 bytes, each instance aligned
         nqw += (int64_t)I.n * I.nw;
         if (I.nw > 1) nwptr += (int64_t)I.m * (I.nw + 1);
         N += I.n;
@@ -382,6 +393,7 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     ix->M = M;
     ix->nqw = nqw;
     ix->nwptr = nwptr;
+    ix->npw = npw;
     ix->maxm = maxm;
     ix->inst_h = inst;
     IndexArrays &d = ix->d;
@@ -522,9 +534,11 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
         APS_TRY(d.crow.alloc((size_t)std::max<int64_t>(nnz, 1), s));
         APS_TRY(d.vmeta.alloc((size_t)std::max<int64_t>(N, 1), s));
         APS_TRY(d.vcand.alloc((size_t)std::max<int64_t>(N, 1), s));
+        APS_TRY(d.pn4.alloc((size_t)std::max<int64_t>(ix->npw, 4), s));
+        APS_CUDA(cudaMemsetAsync(d.pn4.p, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(ix->npw, 4), s));
         k_pack<<<grid_for(std::max(nnz, N), T256), T256, 0, s>>>(d.cptr.p, d.crank.p, d.cval.p, d.len.p, d.split.p,
-                                                                 d.mwpre.p, d.pnorm.p, N, nnz, d.crow.p, d.vmeta.p,
-                                                                 d.vcand.p);
+                                                                 d.mwpre.p, d.pnorm.p, d.vinst.p, d.inst.p, N, nnz,
+                                                                 d.crow.p, d.vmeta.p, d.vcand.p, d.pn4.p);
         APS_LAUNCH_CHECK();
     }
     // ---- join work list

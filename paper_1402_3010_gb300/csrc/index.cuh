@@ -14,6 +14,9 @@
 //               dot(q, x') <= ||x'||_2 for any unit q
 //   vcand[N]    what verification reads of a candidate y, in one 16-byte load: {int32 row
 //               offset, int32 |y'|, float32 maxweight(y'), float32 ||y'||_2 bound}
+//   pn4[]       ||y'||_2 rounded up to a 4-bit code (c * 1.01/15 >= ||y'||_2), eight codes
+//               per 32-bit word, each instance from a 16-byte boundary (word pbase): the join
+//               copies a window's codes into shared memory and rejects candidates with them
 //   post[]      posting entries {int32 local vector id | min(|y|, 255) << 24, float32
 //               weight} (8 bytes), in increasing id inside each list; the size class in
 //               the top byte lets minsize skip an entry without another load (instances
@@ -30,18 +33,23 @@ namespace aps {
 
 constexpr int JOIN_THREADS = 1024;
 constexpr int JOIN_WMAX = 40960;  // accumulator slots of a whole CTA (160 KB)
-constexpr int JOIN_RMAX = 2048;   // dense rank table for dot(x, y') lookups (8 KB)
-constexpr int JOIN_XCAP = 2048;   // x's row kept in shared memory when |x| <= XCAP / G
+constexpr int JOIN_RMAX = 1536;   // dense rank table for dot(x, y') lookups (6 KB)
+constexpr int JOIN_XCAP = 1536;   // x's row kept in shared memory when |x| <= XCAP / G
 // per-warp list of emitted pairs of one window: a warp scans at most W/NW slots rounded
 // up to 128 (W/NW = 1280 for every group shape)
 constexpr int JOIN_ECAP = JOIN_WMAX / (JOIN_THREADS / 32) + 128;
 constexpr int JOIN_STAGE_SLAB = 4096;  // staging slots a query group reserves at a time
+// ||y'||_2 bounds in 4 bits per vector: code c stands for c * PN4_STEP (PN4_STEP = 1.01 / 15,
+// above any norm the index accepts), and PN4_UNIT = PN4_STEP in units of 2^-30, rounded up
+constexpr float PN4_STEP = 1.01f / 15.f;
+constexpr uint32_t PN4_UNIT = 72298617u;
 
 struct InstDesc {
     int64_t vbase;   // first global vector id
     int64_t qwbase;  // first (vector, window) slot of the per-window pair counts
     int64_t wbase;   // first wptr entry (instances with nw > 1)
     int64_t ebase;   // first component (nnz offset)
+    int64_t pbase;   // first 32-bit word of the instance's 4-bit ||y'||_2 codes (a multiple of 4)
     int32_t n;       // vectors
     int32_t m;       // dimensions
     int32_t rbase;   // first global rank
@@ -67,6 +75,7 @@ struct IndexArrays {
     DBuf<int2> crow;
     DBuf<int4> vmeta;
     DBuf<int4> vcand;  // {row offset, |x'|, maxweight(x'), ||x'||_2 bound} per vector
+    DBuf<uint32_t> pn4;  // 4-bit ||x'||_2 codes, eight per word, each instance 16-byte aligned
     DBuf<int32_t> len, split, qsplit;
     DBuf<float> mw, mwpre;
     DBuf<float> pnorm;  // ||x'||_2 of the unindexed prefix (rounded up, with the norm tolerance)
@@ -107,6 +116,7 @@ struct aps_index {
     int64_t nsuf = 0;  // indexed components
     int64_t nqw = 0;   // (vector, window) slots
     int64_t nwptr = 0;
+    int64_t npw = 0;   // words of the 4-bit ||x'||_2 codes
     int32_t maxm = 0;
     float t = 0.f;     // single-instance threshold
     std::vector<aps::InstDesc> inst_h;
@@ -139,7 +149,8 @@ aps_status pairs_to_host(aps_pairs *p, cudaStream_t s);
 struct QueryArrays {
     DBuf<int2> crow;     // {rank, value} per component, rows in rank order
     DBuf<int4> vmeta;
-    DBuf<int4> vcand;  // {row offset, |x'|, maxweight(x'), ||x'||_2 bound} per vector    // {row offset, |q|, 0, 0}
+    DBuf<int4> vcand;  // {row offset, |x'|, maxweight(x'), ||x'||_2 bound} per vector
+    DBuf<uint32_t> pn4;  // 4-bit ||x'||_2 codes, eight per word, each instance 16-byte aligned    // {row offset, |q|, 0, 0}
     DBuf<int32_t> qsplit;
     DBuf<float> mw;
     int64_t nq = 0, nnz = 0;

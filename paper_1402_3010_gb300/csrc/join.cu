@@ -52,6 +52,7 @@ struct JoinParams {
     const int2 *crow;    // rank-ordered rows {rank, value}
     const int4 *vmeta;   // {row offset, |x|, |x'|, maxweight(x')}
     const int4 *vcand;   // {row offset, |y'|, maxweight(y'), ||y'||_2 bound}
+    const uint32_t *pn4; // 4-bit ||y'||_2 codes, eight per word (instance I from word I.pbase)
     const int32_t *qsplit;
     const float *mw;
     const int64_t *lptr;
@@ -81,6 +82,7 @@ constexpr int NWARPS = JOIN_THREADS / 32;
 
 __host__ __device__ constexpr int group_bytes(int G) {
     return 4 * (JOIN_WMAX / G)                       // A
+           + 4 * (JOIN_WMAX / G / 8)                 // the window's 4-bit ||y'||_2 codes
            + 8 * (JOIN_THREADS / G)                  // c_start
            + 4 * (JOIN_THREADS / G)                  // c_cnt
            + 4 * (JOIN_THREADS / G + 4)              // c_ch0
@@ -158,6 +160,14 @@ __device__ __forceinline__ float x_at(int r, const float *xtab, int RG, const in
 // it zero, so every candidate is marked; a few concurrent first adds mark it again, which
 // is harmless); otherwise it only adds where A is already non-zero (remscore). FIRST: the
 // window holds ids at or below x's (slots below lo are skipped).
+// Asynchronous 16-byte global -> shared copy (cp.async, completes out of band) and waits.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // One 128-entry chunk of a segment: entries off .. off + 127 of seg[0, cnt), lane l taking
 // off + l, off + l + 32, ... (see walk_chunks).
 template <bool CREATE, bool FIRST>
@@ -279,7 +289,8 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     const int WG = JOIN_WMAX / G, RG = JOIN_RMAX / G;
     unsigned char *base = smem + (size_t)g * group_bytes(G);
     uint32_t *A = reinterpret_cast<uint32_t *>(base);  // fixed point, units of 2^-30
-    int64_t *c_start = reinterpret_cast<int64_t *>(A + WG);        // [GT]
+    uint32_t *pn4s = A + WG;                                        // [WG / 8], 16-byte aligned
+    int64_t *c_start = reinterpret_cast<int64_t *>(pn4s + WG / 8);  // [GT]
     int32_t *c_cnt = reinterpret_cast<int32_t *>(c_start + GT);    // [GT]
     int32_t *c_ch0 = c_cnt + GT;                                    // [GT + 4] chunk prefix
     float *c_xv = reinterpret_cast<float *>(c_ch0 + GT + 4);        // [GT]
@@ -348,6 +359,11 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
             const int wn = min(I.W, I.n - w0);
             const int lo = max(0, lx + 1 - w0);
             bool created = false;  // any entry of a creating component in this window
+            if (f_upper) {  // the window's 4-bit ||y'||_2 codes into shared memory, behind the accumulation
+                const uint32_t *src = P.pn4 + I.pbase + (w0 >> 3);
+                for (int q = gt; q < (wn + 31) >> 5; q += GT) cp_async16(pn4s + 4 * q, src + 4 * q);
+                cp_async_commit();
+            }
             // ---------------- accumulate. Components are walked creating-first (those with
             // remscore >= t), so every batch holds its creating part before its updating part.
             if (xl <= 32) {
@@ -394,6 +410,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                         else walk_chunks_r<false, false>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
                     }
                 }
+                cp_async_wait_all();  // the window's codes have landed (visible after the barrier)
                 gsync(G, g, GT);
             } else
             for (int c0 = 0; c0 < xl; c0 += GT) {
@@ -470,24 +487,44 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                         else walk_chunks<false, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
                     }
                 }
+                cp_async_wait_all();  // the window's codes have landed (visible after the barrier)
                 gsync(G, g, GT);
             }
             if (!created) continue;  // no candidate can exist in this window
             // ---------------- verify. The creating pass marked every candidate in bm. Each
-            // warp walks its share of bm 32 words (1024 slots) at a time and takes the set
-            // bits in slot order, 32 candidates per batch: lane j of a batch takes the
-            // candidate at position b + j, located from the lanes' popcount prefix. Taken
-            // slots are cleared in A (bm words as they are read), and the emitted (y, score)
-            // go to the warp's scratch list in increasing y.
+            // warp walks its share of bm 32 words (1024 slots) at a time, a word per lane.
+            // First each lane tests its word's candidates against the window's ||y'||_2
+            // codes: since dot(x, y') <= ||y'||_2, a candidate with A[y] + ||y'||_2 <=
+            // t - beta cannot match (most stop here, with no global load; their A is
+            // cleared). Then the remaining bits are taken in slot order, 32 candidates per
+            // batch: lane j of a batch takes the candidate at position b + j, located from
+            // the lanes' popcount prefix. Taken slots are cleared in A (bm words as they are
+            // read), and the emitted (y, score) go to the warp's scratch list in increasing y.
             const int wlo = lo >> 5, whi = (wn + 31) >> 5;
             const int wper = (whi - wlo + NW - 1) / NW;
             const int wb = wlo + gw * wper, we = min(wb + wper, whi);
+            // A[y] + ||y'||_2 <= t - beta in units of 2^-30: threshold rounded down, codes
+            // rounded up, so the test keeps at least every candidate the exact one keeps
+            const uint32_t thq = __float2uint_rd(fmaxf(t - beta, 0.f) * 1073741824.f);
             int ne = 0;
             for (int wq = wb; wq < we; wq += 32) {
                 uint32_t word = 0u;
                 if (wq + lane < we) {
                     word = bm[wq + lane];
                     bm[wq + lane] = 0u;
+                }
+                n_cand += (unsigned long long)__popc(word);
+                if (f_upper) {
+                    const int sb = (wq + lane) << 5;
+                    uint32_t keep = 0u;
+                    for (uint32_t wv = word; wv; wv &= wv - 1u) {
+                        const int b = __ffs(wv) - 1;
+                        const int sl = sb + b;
+                        const uint32_t a = A[sl];
+                        const uint32_t code = (pn4s[sl >> 3] >> ((sl & 7) << 2)) & 15u;
+                        if (a + code * PN4_UNIT > thq) keep |= 1u << b; else A[sl] = 0u;
+                    }
+                    word = keep;
                 }
                 const int c = __popc(word);
                 int T;
@@ -584,7 +621,6 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     const unsigned bal = __ballot_sync(0xffffffffu, emit);
                     if (emit) elist[ne + __popc(bal & lt_mask)] = make_int2(w0 + s, __float_as_int(sc));
                     ne += __popc(bal);
-                    n_cand += have ? 1ull : 0ull;
                 }
             }
             if (lane == 0) wcnt[gw] = ne;
@@ -823,6 +859,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
             P.crow = d.crow.p;
             P.vmeta = d.vmeta.p;
             P.vcand = d.vcand.p;
+            P.pn4 = d.pn4.p;
             P.qsplit = d.qsplit.p;
             P.mw = d.mw.p;
             P.lptr = d.lptr.p;
@@ -1057,6 +1094,7 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
         P.crow = d.crow.p;
         P.vmeta = d.vmeta.p;
         P.vcand = d.vcand.p;
+        P.pn4 = d.pn4.p;
         P.qsplit = d.qsplit.p;
         P.mw = d.mw.p;
         P.lptr = d.lptr.p;
@@ -1166,6 +1204,7 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
             P.crow = d.crow.p;
             P.vmeta = d.vmeta.p;
             P.vcand = d.vcand.p;
+            P.pn4 = d.pn4.p;
             P.qsplit = d.qsplit.p;
             P.mw = d.mw.p;
             P.lptr = d.lptr.p;
