@@ -19,6 +19,8 @@ is not sharded across GPUs); the value is all ranks' evaluations / max time.
 from __future__ import annotations
 
 import argparse
+import copy
+import gc
 import json
 import math
 import os
@@ -68,6 +70,10 @@ def parse():
                          "embedding self-join on the tensor cores; batched: 512 independent sparse "
                          "instances; serving: query batches against a 1M-vector resident index")
     ap.add_argument("--serve-batches", type=int, default=160)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="default workload: print the sparse headline only, without the dense, batched, serving "
+                         "and small-instance records under 'forms'")
+    ap.add_argument("--form-steps", type=int, default=5, help="timed steps of each record under 'forms'")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--d", type=int, default=256)
     return ap.parse_args()
@@ -231,6 +237,37 @@ def replica_value(evals_per_replica: int, steps: int, world: int, ms: float) -> 
     return world * evals_per_replica * steps / (ms * 1e-3)
 
 
+class no_gc:
+    """Keep Python's garbage collector out of a timed region (a collection of this process's
+    many objects can take tens of milliseconds): collect first, disable, re-enable after."""
+
+    def __enter__(self):
+        gc.collect()
+        self.was = gc.isenabled()
+        gc.disable()
+
+    def __exit__(self, *exc):
+        if self.was:
+            gc.enable()
+
+
+def measured_profile(profile: str, source: str, t: float):
+    """The committed ncu record of a kernel (profiles/<profile>) when the kernel source is
+    byte-identical to the one the counters were taken from, else None."""
+    import hashlib
+
+    prof = os.path.join(ROOT, "profiles", profile)
+    if not os.path.exists(prof):
+        return None
+    with open(prof) as f:
+        tr = json.load(f)
+    with open(os.path.join(ROOT, "paper_1402_3010_gb300", "csrc", source), "rb") as f:
+        cur = hashlib.sha1(f.read()).hexdigest()[:16]
+    if tr.get("source_sha1_16") == cur and abs(tr.get("t", -1) - t) < 1e-7:
+        return tr
+    return None
+
+
 def measured_traffic(profile: str, source: str, t: float):
     """DRAM bytes per launch from a committed ncu capture (profiles/<profile>), valid only
     while the kernel source is byte-identical to the one the counters were taken from."""
@@ -300,14 +337,15 @@ def run_aps(args, rank, world):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        st, cnt = step()
-        stats.append(st)
-        join_ms.append(st["ms_join"])
-    e1.record(stream)
-    barrier()
+    with no_gc():
+        e0.record(stream)
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            st, cnt = step()
+            stats.append(st)
+            join_ms.append(st["ms_join"])
+        e1.record(stream)
+        barrier()
     launches = aps.aps_launch_count() - l0
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
@@ -343,13 +381,14 @@ def run_aps(args, rank, world):
             e2e_step()
         del gpu_ms[:]
         barrier()
-        t0 = time.perf_counter()
-        outs, marks = [], []
-        for _ in range(args.e2e_steps):
-            outs.append(e2e_step())
-            marks.append(time.perf_counter())
-        barrier()
-        dt = time.perf_counter() - t0
+        with no_gc():
+            t0 = time.perf_counter()
+            outs, marks = [], []
+            for _ in range(args.e2e_steps):
+                outs.append(e2e_step())
+                marks.append(time.perf_counter())
+            barrier()
+            dt = time.perf_counter() - t0
         steps_ms = [round(1e3 * (b - a), 2) for a, b in zip([t0] + marks[:-1], marks)]
         dt = max_over_ranks(dt * 1e3, dev, world) * 1e-3  # the slowest rank's end-to-end time
         e2e = {"value": world * evals * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": hbytes,
@@ -367,7 +406,8 @@ def run_aps(args, rank, world):
     alg_bytes = 8 * last["visits"] + 8 * last["candidates"] + 16 * last["verified"] + 8 * last["pairs"]
     jm = statistics.mean(join_ms)
     achieved = alg_bytes / (jm * 1e-3) / 1e9
-    traffic = measured_traffic("join_kernel_traffic.json", "join.cu", t) if (c.n, c.m) == (200_000, 100_000) else None
+    prof = measured_profile("join_kernel_traffic.json", "join.cu", t) if (c.n, c.m) == (200_000, 100_000) else None
+    traffic = prof.get("dram_bytes_per_launch") if prof else None
     line = {
         "metric": METRIC,
         "value": replica_value(evals, args.steps, world, ms),
@@ -400,6 +440,12 @@ def run_aps(args, rank, world):
             "traffic": traffic,
             "alg_bytes_per_launch": alg_bytes,
             "ms_per_launch": jm,
+            # measured DRAM bytes of one launch (ncu, same source) over the launch time, against
+            # the same peak; the index is L2-resident, so this is far below the effective figure
+            "dram_gbs": traffic / (jm * 1e-3) / 1e9 if traffic else None,
+            "dram_frac": traffic / (jm * 1e-3) / 1e9 / peak if traffic else None,
+            "bound_by": prof.get("bound_by") if prof else None,
+            "counters": prof.get("counters") if prof else None,
         },
         "phases_ms": {"build": last["ms_build"], "join": last["ms_join"], "output": last["ms_sort"],
                       "join_call": last["ms_total"]},
@@ -460,13 +506,14 @@ def run_dense(args, rank, world):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        st, cnt = step()
-        gemm_ms.append(st["ms_join"])
-    e1.record(stream)
-    barrier()
+    with no_gc():
+        e0.record(stream)
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            st, cnt = step()
+            gemm_ms.append(st["ms_join"])
+        e1.record(stream)
+        barrier()
     launches = aps.aps_launch_count() - l0
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
@@ -488,10 +535,11 @@ def run_dense(args, rank, world):
 
         e2e_step()
         barrier()
-        t0 = time.perf_counter()
-        outs = [e2e_step() for _ in range(args.e2e_steps)]
-        barrier()
-        dt = time.perf_counter() - t0
+        with no_gc():
+            t0 = time.perf_counter()
+            outs = [e2e_step() for _ in range(args.e2e_steps)]
+            barrier()
+            dt = time.perf_counter() - t0
         dt = max_over_ranks(dt * 1e3, dev, world) * 1e-3
         e2e = {"value": world * evals * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": X.nbytes,
                "d2h_bytes_per_step": int(max(outs)) * 12, "ms_per_step": 1000 * dt / args.e2e_steps}
@@ -565,6 +613,37 @@ def dense_precision(X, t, rows, gi, gj, gs, ref, band=1e-5):
             "extra_outside_band": e_out, "extra_in_band": len(extra) - e_out, "band": band}
 
 
+def sparse_dot64(q, c, a, b):
+    """float64 dot product of row a of q with row b of c (sparse rows, sorted ids)."""
+    ia, va = q.row(int(a))
+    ib, vb = c.row(int(b))
+    _, pa, pb = np.intersect1d(ia, ib, assume_unique=True, return_indices=True)
+    return float(np.dot(va[pa].astype(np.float64), vb[pb].astype(np.float64)))
+
+
+def agreement(i, j, s, ref, t, n, dot64, band=1e-5):
+    """A result against the oracle's pairs: pairs only one side has, split by whether their
+    float64 score (recomputed from the inputs for pairs only the path reports) lies within
+    `band` of t (only those may differ), and max |score - fp64| over the common pairs."""
+    keys = np.asarray(i, np.int64) * n + np.asarray(j, np.int64)
+    rk = ref.keys(n)
+    gpu_only = np.setdiff1d(keys, rk)
+    ref_only = np.setdiff1d(rk, keys)
+    rmap = dict(zip(rk.tolist(), np.asarray(ref.s, np.float64).tolist()))
+    missing = [rmap[k] for k in ref_only.tolist()]
+    extra = [dot64(*divmod(k, n)) for k in gpu_only.tolist()]
+    common = np.intersect1d(keys, rk)
+    err = 0.0
+    if common.size:
+        gs = np.asarray(s, np.float64)[np.searchsorted(keys, common)]
+        err = float(np.abs(gs - np.asarray(ref.s, np.float64)[np.searchsorted(rk, common)]).max())
+    return {"pairs_checked": int(common.size), "max_abs_err": err,
+            "missing_outside_band": int(sum(abs(v - t) > band for v in missing)),
+            "missing_in_band": int(sum(abs(v - t) <= band for v in missing)),
+            "extra_outside_band": int(sum(abs(v - t) > band for v in extra)),
+            "extra_in_band": int(sum(abs(v - t) <= band for v in extra)), "band": band}
+
+
 BATCHED_WORKLOAD = ("batched sparse all-pairs: 512 independent instances, n log-uniform in [100, 20000], m=50000, "
                     "|x| ~ Poisson(30) in [1,300], Zipf(1.1) ids, U(0,1] weights, t ~ U(0.6, 0.9)")
 SERVING_WORKLOAD = ("serving: resident index of 1M sparse vectors (m=200000, power-law |x| mean 40, Zipf(1.0), "
@@ -625,13 +704,14 @@ def run_batched(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        st, cnt = step()
-        jm.append(st["ms_join"])
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
+    with no_gc():
+        e0.record(stream)
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            st, cnt = step()
+            jm.append(st["ms_join"])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
     launches = aps.aps_launch_count() - l0
     clk = clocks.stop()
@@ -653,17 +733,34 @@ def run_batched(args):
         sel = np.random.default_rng(11).choice(len(ns), 24, replace=False)
         t0 = time.perf_counter()
         ev = 0
+        refs = {}
         for r in sel:
             a, b = int(ro[r]), int(ro[r + 1])
             ip_r = c.indptr[a:b + 1] - c.indptr[a]
             cr = synth.SparseCSR(ip_r, c.idx[c.indptr[a]:c.indptr[b]], c.val[c.indptr[a]:c.indptr[b]], b - a,
                                  int(m[r]))
-            oracle.all_pairs(cr, float(t[r]), oracle.ALL_PAIRS_2)
+            refs[int(r)] = (cr, oracle.all_pairs(cr, float(t[r]), oracle.ALL_PAIRS_2)[0])
             ev += (b - a) * (b - a - 1) // 2
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"sequential all-pairs-2 (C, FP64) on 24 random instances ({ev} "
                                           f"evaluations) in {dt:.2f} s"}
+        # the same instances' pairs from one more (untimed) call of the path
+        outs, _ = aps.aps_batch_all_pairs_csr(ro, ip, ix, vv, m, t, 0, stream)
+        try:
+            acc = {"instances": len(refs), "pairs_checked": 0, "max_abs_err": 0.0, "missing_outside_band": 0,
+                   "missing_in_band": 0, "extra_outside_band": 0, "extra_in_band": 0, "band": 1e-5}
+            for r, (cr, ref) in refs.items():
+                gi, gj, gs = aps.pairs_to_numpy(outs[r])
+                ag = agreement(gi, gj, gs, ref, float(t[r]), max(cr.n, 1), lambda a, b: sparse_dot64(cr, cr, a, b))
+                for k in ("pairs_checked", "missing_outside_band", "missing_in_band", "extra_outside_band",
+                          "extra_in_band"):
+                    acc[k] += ag[k]
+                acc["max_abs_err"] = max(acc["max_abs_err"], ag["max_abs_err"])
+        finally:
+            for o in outs:
+                aps.aps_pairs_free(o)
+        line["accuracy"] = acc
     return line
 
 
@@ -723,30 +820,192 @@ def run_serving(args):
     run(None)  # warm-up
     clocks = Clocks(0)
     clocks.start()
-    tsat, lsat, pairs = run(None)
+    with no_gc():
+        tsat, lsat, pairs = run(None)
     clk = clocks.stop()
     qps = offs[-1] / tsat
     loads = {}
     for frac in (0.5, 0.8):
         gaps = np.random.default_rng(58).exponential(1.0 / (frac * len(batches) / tsat), size=len(batches))
-        tt, ll, _ = run(np.cumsum(gaps))
+        with no_gc():
+            tt, ll, _ = run(np.cumsum(gaps))
         loads[f"{int(frac * 100)}%"] = {"p50_ms": 1000 * float(np.percentile(ll, 50)),
                                         "p99_ms": 1000 * float(np.percentile(ll, 99)),
                                         "batches_per_s": len(batches) / tt}
-    aps.aps_index_free(h)
+    # the joins' algorithmic bytes: every batch once more through aps_query (untimed), its work
+    # counters summed, over the saturated serving time
+    work = {"visits": 0, "candidates": 0, "verified": 0, "pairs": 0, "band": 0}
+    for ip, ix, vv, nq in batches:
+        p = aps.aps_query(h, ip, ix, vv, nq, t)
+        aps.aps_pairs_free(p)
+        st = aps.aps_index_stats(h)
+        for k in work:
+            work[k] += int(st[k])
     evals = int(offs[-1]) * c.n
-    return {
+    h2d = sum(ip.nbytes + ix.nbytes + vv.nbytes for ip, ix, vv, _ in batches)
+    line = {
         "metric": METRIC, "value": evals / tsat, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": 1000 * tsat, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded generator, no dataset)",
         "config": {"workload": SERVING_WORKLOAD, "index_n": c.n, "index_nnz": c.nnz, "batches": len(batches),
                    "queries": int(offs[-1]), "slots": args.slots, "t": t, "parallelism": "single GPU",
-                   "pairs": pairs, "tiles": aps.aps_get_tuning(query=True)},
+                   "pairs": pairs, "tiles": aps.aps_get_tuning(query=True),
+                   "step": "all batches submitted at once and polled to completion (saturated)"},
+        "roofline": _sparse_roofline(work, 1000 * tsat),
+        "work": work,
         "serving": {"saturated_queries_per_s": qps,
                     "saturated_p50_ms": 1000 * float(np.percentile(lsat, 50)),
                     "saturated_p99_ms": 1000 * float(np.percentile(lsat, 99)), "poisson_load": loads},
-        "clocks": clk, "e2e": None,
+        "clocks": clk,
+        # the serving loop is end to end already: host query CSR in at submit, host pairs out at poll
+        "e2e": {"value": evals / tsat, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(pairs) * 12, "ms_per_step": 1000 * tsat},
     }
+    line["roofline"]["note"] = ("algorithmic bytes of every batch's join (counters from one untimed pass) over "
+                                "the saturated serving time, host submission and polling included")
+    if not args.no_cpu_baseline:
+        import oracle
+
+        qs_ = batches[0]
+        k = min(16, qs_[3])
+        sub = synth.SparseCSR(qs_[0][:k + 1].copy(), qs_[1][:qs_[0][k]], qs_[2][:qs_[0][k]], k, c.m)
+        t0 = time.perf_counter()
+        ref = oracle.bruteforce_cross(sub, c, t)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": k * c.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"float64 brute force (C) of {k} queries against the {c.n}-vector index "
+                                          f"({k * c.n} evaluations) in {dt:.2f} s"}
+        p = aps.aps_query(h, sub.indptr, sub.idx, sub.val, k, t)
+        try:
+            gi, gj, gs = aps.pairs_to_numpy(p)
+        finally:
+            aps.aps_pairs_free(p)
+        line["accuracy"] = dict(agreement(gi, gj, gs, ref, t, c.n, lambda a, b: sparse_dot64(sub, c, a, b)),
+                                queries=k)
+    aps.aps_index_free(h)
+    return line
+
+
+SMALL_WORKLOAD = ("plain sparse all-pairs: n=2000, m=5000, |x| ~ Poisson(20) in [1,200], Zipf(1.1) ids, U(0,1] "
+                  "weights, L2-normalised, FP32, t=0.7")
+
+
+def run_small(args):
+    """The 2,000-vector set, a latency case (its 40k components and 320 KB index fit in L2):
+    time per call through the C ABI from a device CSR to device pairs (index build + join +
+    output), and per join of a built index (its join phase replayed from a CUDA graph)."""
+    import torch
+
+    import paper_1402_3010_gb300 as aps
+    import synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    aps.load()
+    c, t = synth.config_small(seed=1)
+    t = float(np.float32(t))
+    stream = torch.cuda.current_stream(dev)
+    ip, ix, vv = (torch.from_numpy(a).to(dev) for a in (c.indptr, c.idx, c.val))
+    evals = c.n * (c.n - 1) // 2
+    K = 200
+
+    def call():
+        h = aps.aps_build_index(ip, ix, vv, c.n, c.m, t, 0, stream)
+        p = aps.aps_all_pairs(h)
+        n = int(p.count)
+        aps.aps_pairs_free(p)
+        st = aps.aps_index_stats(h)
+        aps.aps_index_free(h)
+        return st, n
+
+    for _ in range(5):
+        call()
+    clocks = Clocks(0)
+    clocks.start()
+    lat = []
+    l0 = aps.aps_launch_count()
+    with no_gc():
+        torch.cuda.synchronize(dev)
+        for _ in range(K):
+            t0 = time.perf_counter()
+            st, cnt = call()
+            lat.append(1e3 * (time.perf_counter() - t0))
+    launches = (aps.aps_launch_count() - l0) / K
+    h = aps.aps_build_index(ip, ix, vv, c.n, c.m, t, 0, stream)
+    jl, jms = [], []
+    with no_gc():
+        for _ in range(K):
+            t0 = time.perf_counter()
+            p = aps.aps_all_pairs(h)
+            aps.aps_pairs_free(p)
+            jl.append(1e3 * (time.perf_counter() - t0))
+            jms.append(aps.aps_index_stats(h)["ms_join"])
+    stj = aps.aps_index_stats(h)
+    aps.aps_index_free(h)
+    clk = clocks.stop()
+    ms = statistics.mean(lat)
+    rl = _sparse_roofline(stj, statistics.mean(jms))
+    rl["bound"] = "latency"
+    rl["note"] = "40k components, a 320 KB index: launch and latency bound, the HBM fraction is not the measure"
+    line = {
+        "metric": METRIC, "value": evals / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": 5,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": SMALL_WORKLOAD, "n": c.n, "m": c.m, "nnz": c.nnz, "t": t, "parallelism": "single GPU",
+                   "pairs_per_step": cnt, "evaluations_per_step": evals,
+                   "l2": "not flushed: a latency case whose inputs are meant to stay on chip"},
+        "latency_ms": {"call_p50": float(np.percentile(lat, 50)), "call_p99": float(np.percentile(lat, 99)),
+                       "join_call_p50": float(np.percentile(jl, 50)), "join_call_p99": float(np.percentile(jl, 99)),
+                       "join_kernel_mean": statistics.mean(jms)},
+        "roofline": rl, "work": {k: stj[k] for k in ("visits", "candidates", "verified", "pairs", "band")},
+        "phases_ms": {"build": st["ms_build"], "join": st["ms_join"], "output": st["ms_sort"]},
+        "gpu_launches": launches, "gpu_launches_unit": "kernel launches per call", "clocks": clk, "e2e": None,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+
+        t0 = time.perf_counter()
+        oracle.all_pairs(c, t, oracle.ALL_PAIRS_2)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"sequential all-pairs-2 (C, FP64) over the whole set in {dt * 1e3:.1f} ms"}
+        ref = oracle.bruteforce(c, t)
+        p = aps.aps_build_index(ip, ix, vv, c.n, c.m, t, 0, stream)
+        try:
+            q = aps.aps_all_pairs(p)
+            gi, gj, gs = aps.pairs_to_numpy(q)
+            aps.aps_pairs_free(q)
+        finally:
+            aps.aps_index_free(p)
+        line["accuracy"] = agreement(gi, gj, gs, ref, t, c.n, lambda a, b: sparse_dot64(c, c, a, b))
+    return line
+
+
+FORM_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "dtype", "config", "roofline", "latency_ms",
+             "phases_ms", "work", "serving", "tiles", "clocks", "cpu_baseline", "accuracy", "precision_vs_fp64",
+             "e2e", "gpu_launches", "gpu_launches_unit")
+
+
+def as_form(line):
+    """A full bench line as a record under the headline's 'forms'."""
+    return {k: line[k] for k in FORM_KEYS if k in line and line[k] is not None}
+
+
+def run_forms(args):
+    """The dense, batched, serving and small-instance forms measured beside the headline, on
+    the same GPU in the same run (each with its own clocks, roofline, oracle baseline and
+    accuracy against the oracle)."""
+    a = copy.copy(args)
+    a.steps, a.warmup, a.e2e_steps = args.form_steps, 3, 2
+    forms = {}
+    for name, fn in (("small", lambda: run_small(a)), ("dense", lambda: run_dense(a, 0, 1)),
+                     ("batched", lambda: run_batched(a)), ("serving", lambda: run_serving(a))):
+        t0 = time.perf_counter()
+        rec = as_form(fn())
+        rec["seconds"] = round(time.perf_counter() - t0, 1)
+        forms[name] = rec
+        gc.collect()
+    return forms
 
 
 def run_reference(args, rank):
@@ -1135,6 +1394,8 @@ def main():
         line = run_vertical(args, rank, world)
     else:
         line = run_aps(args, rank, world)
+        if line is not None and world == 1 and not args.no_forms and args.workload == "sparse":
+            line["forms"] = run_forms(args)
     if line is not None:
         print(json.dumps(line), flush=True)
     if world > 1 and args.impl == "aps":
