@@ -30,6 +30,7 @@ __all__ = [
     "config_large",
     "config_dense",
     "config_batched",
+    "config_batched_matches",
     "config_serving",
     "dense_mixture",
     "power_law_lengths",
@@ -322,6 +323,33 @@ def config_batched_csr(seed: int = 4, k: int = 512, n_lo: int = 100, n_hi: int =
         return SparseCSR(np.concatenate([c.indptr, ro, ts.view(np.int32).astype(np.int64)]), c.idx, c.val, N, m)
 
     z = _cached(f"batched-v1-s{seed}-k{k}-{n_lo}-{n_hi}-m{m}", make)
+    N = z.n
+    indptr = z.indptr[: N + 1]
+    ro = z.indptr[N + 1 : N + 2 + k]
+    ts = z.indptr[N + 2 + k :].astype(np.int32).view(np.float32)
+    c = SparseCSR(indptr, z.idx, z.val, N, m)
+    return ro, c, np.full(k, m, dtype=np.int32), ts
+
+
+def config_batched_matches(seed: int = 6, k: int = 512, n_lo: int = 100, n_hi: int = 20000, m: int = 50_000):
+    """A second batched set, one that yields matches: the same instance sizes (n log-uniform
+    in [n_lo, n_hi]) and thresholds t ~ U(0.6, 0.9), but vectors from the large set's family
+    (|x| power law with mean ~50 on [1, 300], Zipf(1.0) ids, log-normal(0,1) weights), so
+    that many vectors share their dominant dimensions. Same return form as
+    config_batched_csr: (row_offsets, SparseCSR, m[k], t[k])."""
+
+    def make():
+        rng = np.random.default_rng(seed)
+        ns = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=k)).astype(np.int64)
+        ts = rng.uniform(0.6, 0.9, size=k).astype(np.float32)
+        N = int(ns.sum())
+        lengths = power_law_lengths(rng, N, ALPHA_MEAN50, 1, 300)
+        c = sparse_vectors(N, m, lengths, 1.0, "lognormal", seed, rng=rng)
+        ro = np.zeros(k + 1, dtype=np.int64)
+        np.cumsum(ns, out=ro[1:])
+        return SparseCSR(np.concatenate([c.indptr, ro, ts.view(np.int32).astype(np.int64)]), c.idx, c.val, N, m)
+
+    z = _cached(f"batchedm-v1-s{seed}-k{k}-{n_lo}-{n_hi}-m{m}", make)
     N = z.n
     indptr = z.indptr[: N + 1]
     ro = z.indptr[N + 1 : N + 2 + k]

@@ -48,3 +48,35 @@ def compare(i, j, s, ref, t, n, *, band=1e-5, tol=1e-5, self_join=True, csr=None
     assert err <= tol, f"score error {err} > {tol}"
     return {"pairs": int(keys.size), "ref": int(rk.size), "max_err": float(err),
             "gpu_only": int(gpu_only.size), "ref_only": int(ref_only.size)}
+
+
+def compare_large(i, j, s, ri, rj, rs, t, n, dot64, *, band=1e-5, tol=1e-5, self_join=True):
+    """compare() for large sets, vectorised: (i, j, s) from the CUDA path, (ri, rj, rs) the
+    oracle's pairs sorted by (i, j). Pairs only one side has must lie within `band` of t by
+    their float64 score (recomputed with dot64(a, b) for the CUDA path's extras); scores of
+    the common pairs within `tol` of the oracle's."""
+    keys = np.asarray(i, np.int64) * n + np.asarray(j, np.int64)
+    rk = np.asarray(ri, np.int64) * n + np.asarray(rj, np.int64)
+    assert np.all(keys[1:] > keys[:-1]), "pairs must be strictly increasing in (i, j)"
+    if self_join:
+        assert np.all(np.asarray(i) < np.asarray(j)), "self-join pairs must have i < j"
+    rs = np.asarray(rs, np.float64)
+    s = np.asarray(s, np.float64)
+    pos = np.searchsorted(rk, keys)
+    pos_c = np.minimum(pos, max(rk.size - 1, 0))
+    hit = (pos < rk.size) & (rk[pos_c] == keys) if rk.size else np.zeros(keys.size, bool)
+    extra = keys[~hit]
+    rpos = np.searchsorted(keys, rk)
+    rpos_c = np.minimum(rpos, max(keys.size - 1, 0))
+    rhit = (rpos < keys.size) & (keys[rpos_c] == rk) if keys.size else np.zeros(rk.size, bool)
+    missing = ~rhit
+    assert np.all(np.abs(rs[missing] - t) <= band), \
+        f"{int(missing.sum())} missing pairs, e.g. {divmod(int(rk[missing][0]), n)} score {rs[missing][0]}"
+    for k in extra.tolist():
+        a, b = divmod(k, n)
+        sc = dot64(a, b)
+        assert abs(sc - t) <= band, f"extra pair {(a, b)} float64 score {sc} (t={t})"
+    err = float(np.abs(s[hit] - rs[pos_c[hit]]).max()) if hit.any() else 0.0
+    assert err <= tol, f"score error {err} > {tol}"
+    return {"pairs": int(keys.size), "ref": int(rk.size), "max_err": err, "gpu_only": int(extra.size),
+            "ref_only": int(missing.sum())}
