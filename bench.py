@@ -784,6 +784,8 @@ def run_serving(args):
         ip = (q.indptr[a:b + 1] - q.indptr[a]).astype(np.int64)
         batches.append((ip, q.idx[q.indptr[a]:q.indptr[b]].copy(), q.val[q.indptr[a]:q.indptr[b]].copy(), int(b - a)))
 
+    overlap = {}
+
     def run(arrivals):
         """Submit batch k at arrivals[k] seconds (all at once when None); latency = result
         in host memory - arrival."""
@@ -813,6 +815,9 @@ def run_serving(args):
                 if not done:
                     time.sleep(0.0001)
             total = time.perf_counter() - t0
+            st = aps.aps_server_timeline(sv)
+            overlap.clear()
+            overlap.update(st, overlap_frac=st["overlap_ms"] / st["busy_ms"] if st["busy_ms"] > 0 else 0.0)
         finally:
             aps.aps_server_free(sv)
         return total, np.array(lat), pairs
@@ -823,6 +828,7 @@ def run_serving(args):
     with no_gc():
         tsat, lsat, pairs = run(None)
     clk = clocks.stop()
+    overlap_sat = dict(overlap)
     qps = offs[-1] / tsat
     loads = {}
     for frac in (0.5, 0.8):
@@ -831,7 +837,9 @@ def run_serving(args):
             tt, ll, _ = run(np.cumsum(gaps))
         loads[f"{int(frac * 100)}%"] = {"p50_ms": 1000 * float(np.percentile(ll, 50)),
                                         "p99_ms": 1000 * float(np.percentile(ll, 99)),
-                                        "batches_per_s": len(batches) / tt}
+                                        "batches_per_s": len(batches) / tt,
+                                        "overlap_frac": overlap.get("overlap_frac"),
+                                        "max_in_flight": overlap.get("max_in_flight")}
     # the joins' algorithmic bytes: every batch once more through aps_query (untimed), its work
     # counters summed, over the saturated serving time
     work = {"visits": 0, "candidates": 0, "verified": 0, "pairs": 0, "band": 0}
@@ -855,7 +863,9 @@ def run_serving(args):
         "work": work,
         "serving": {"saturated_queries_per_s": qps,
                     "saturated_p50_ms": 1000 * float(np.percentile(lsat, 50)),
-                    "saturated_p99_ms": 1000 * float(np.percentile(lsat, 99)), "poisson_load": loads},
+                    "saturated_p99_ms": 1000 * float(np.percentile(lsat, 99)), "poisson_load": loads,
+                    # device time with two or more batches in flight / device time with any
+                    "overlap_frac": overlap_sat.get("overlap_frac"), "device_timeline_ms": overlap_sat},
         "clocks": clk,
         # the serving loop is end to end already: host query CSR in at submit, host pairs out at poll
         "e2e": {"value": evals / tsat, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

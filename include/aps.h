@@ -381,6 +381,22 @@ aps_status aps_stream_poll(aps_server *server, uint64_t ticket, int32_t timeout_
  * dropped; the next poll returns APS_ECANCELED. Errors: APS_EINVAL (NULL server, an
  * unknown ticket). */
 aps_status aps_stream_cancel(aps_server *server, uint64_t ticket);
+/* The device time line of a server's completed batches (continuous batching, Alg. 6's
+ * matching step run for several query batches at once). Each batch's device work -- its
+ * query upload, preparation, join and result download on its slot's stream -- lies between
+ * two CUDA events; busy_ms is the device time with at least one batch in flight,
+ * overlap_ms the time with two or more (admitted batches running side by side), span_ms
+ * from the first batch's start to the last one's end, max_in_flight the most batches in
+ * flight at once. Errors: APS_EINVAL (NULL arguments). */
+typedef struct aps_timeline {
+    int64_t batches;       /* completed batches (failed ones are not counted) */
+    double busy_ms;
+    double overlap_ms;
+    double span_ms;
+    int32_t max_in_flight;
+    int32_t _reserved;
+} aps_timeline;
+aps_status aps_server_timeline(aps_server *server, aps_timeline *out);
 void aps_server_free(aps_server *server);
 
 /* ---- misc ----------------------------------------------------------------------- */

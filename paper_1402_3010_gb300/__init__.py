@@ -100,6 +100,14 @@ class aps_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class aps_timeline(ctypes.Structure):
+    _fields_ = [("batches", _i64), ("busy_ms", ctypes.c_double), ("overlap_ms", ctypes.c_double),
+                ("span_ms", ctypes.c_double), ("max_in_flight", _i32), ("_reserved", _i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("_")}
+
+
 class aps_instance(ctypes.Structure):
     _fields_ = [("indptr", _P), ("idx", _P), ("val", _P), ("n", _i32), ("m", _i32), ("t", _f32),
                 ("_reserved", _i32)]
@@ -162,6 +170,7 @@ def load():
             "aps_stream_poll": (_i32, [_P, _u64, _i32, ctypes.POINTER(aps_pairs)]),
             "aps_stream_cancel": (_i32, [_P, _u64]),
             "aps_server_free": (None, [_P]),
+            "aps_server_timeline": (_i32, [_P, ctypes.POINTER(aps_timeline)]),
             "aps_last_error": (ctypes.c_char_p, []),
             "aps_version": (ctypes.c_char_p, []),
             "aps_debug_fail_alloc": (None, [_i64]),
@@ -515,6 +524,14 @@ def aps_stream_poll(server: int, ticket: int, timeout_us: int = 0):
 
 def aps_stream_cancel(server: int, ticket: int) -> None:
     _check(load().aps_stream_cancel(server, int(ticket)), "aps_stream_cancel")
+
+
+def aps_server_timeline(server: int) -> dict:
+    """The device time line of the server's completed batches: batches, busy_ms (at least
+    one batch in flight), overlap_ms (two or more), span_ms, max_in_flight."""
+    st = aps_timeline()
+    _check(load().aps_server_timeline(server, ctypes.byref(st)), "aps_server_timeline")
+    return st.as_dict()
 
 
 def aps_server_free(server: int) -> None:

@@ -43,6 +43,11 @@ aps_status dalloc(void **p, size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
 // Host-side fault injection for tests: fail the k-th next allocation (k >= 1), 0 = off.
 void set_alloc_fault(int64_t k);
+// Pinned host blocks for results copied to the host, recycled through a process-wide cache
+// (page-locking fresh memory for every result costs far more than the copy itself). Sizes
+// are rounded up to a power of two of at least 1 MiB; at most 8 GiB is kept cached.
+aps_status halloc(void **p, size_t bytes);
+void hfree(void *p, size_t bytes);
 
 template <class T>
 struct DBuf {

@@ -615,12 +615,14 @@ __global__ void k_q_split(const int64_t *__restrict__ qptr, const int2 *__restri
 }  // namespace
 
 aps_status prepare_queries(const aps_index *ix, const int64_t *qptr, const int32_t *qidx, const float *qval,
-                           int32_t nq, float t, uint32_t flags, cudaStream_t s, QueryArrays &qa) {
+                           int32_t nq, float t, uint32_t flags, cudaStream_t s, QueryArrays &qa, int64_t nnz_known) {
     const IndexArrays &d = ix->d;
-    int64_t nnz = 0, first = 0;
-    APS_CUDA(cudaMemcpyAsync(&nnz, qptr + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    APS_CUDA(cudaMemcpyAsync(&first, qptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    APS_CUDA(cudaStreamSynchronize(s));
+    int64_t nnz = nnz_known, first = 0;
+    if (nnz_known < 0) {  // the row pointers live on the device only: read their ends back
+        APS_CUDA(cudaMemcpyAsync(&nnz, qptr + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        APS_CUDA(cudaMemcpyAsync(&first, qptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        APS_CUDA(cudaStreamSynchronize(s));
+    }
     if (first != 0 || nnz < 0 || nnz >= (1ll << 31)) {
         set_error("query indptr[0] must be 0 and nnz in [0, 2^31)");
         return APS_EINVAL;

@@ -25,6 +25,7 @@
 //               only for instances with > 1 window
 #pragma once
 
+#include <atomic>
 #include <mutex>
 
 #include "aps_internal.cuh"
@@ -126,6 +127,9 @@ struct aps_index {
     int64_t class_begin[5] = {0, 0, 0, 0, 0};  // classes G = 1, 2, 4, 8
     // output sizing from the previous join
     int64_t hint_pairs = 0;
+    // pairs per query (times 16) that query batches on this index have needed at most: the
+    // first staging of the next batch is sized from it, so that it rarely runs twice
+    mutable std::atomic<int64_t> q_ppq16{64 * 16};
     aps::JoinGraph jgraph;  // the join phase, replayed by every join of this index
     aps_stats stats{};
     mutable std::mutex stats_mu;  // queries may run concurrently (serving slots)
@@ -135,6 +139,7 @@ namespace aps {
 
 struct PairsAlloc {          // bookkeeping behind aps_pairs._priv
     void *block = nullptr;   // one allocation holding i, j and score
+    size_t bytes = 0;        // its size (host blocks go back to the pinned cache)
     cudaStream_t stream = nullptr;
     int on_device = 1;
     int refs = 1;            // aps_pairs views sharing the block (batched results)
@@ -156,8 +161,11 @@ struct QueryArrays {
     int64_t nq = 0, nnz = 0;
 };
 
+// nnz_known: the number of components when the caller knows it from host row pointers
+// (qptr[0] = 0 checked there), else -1 (both ends are then read back from the device).
 aps_status prepare_queries(const aps_index *ix, const int64_t *qptr, const int32_t *qidx, const float *qval,
-                           int32_t nq, float t, uint32_t flags, cudaStream_t s, QueryArrays &qa);
+                           int32_t nq, float t, uint32_t flags, cudaStream_t s, QueryArrays &qa,
+                           int64_t nnz_known = -1);
 
 // Match prepared queries against every indexed vector: pairs (query row, vector id, score)
 // with score >= t, sorted by (query, vector). Safe to call concurrently on different

@@ -963,7 +963,7 @@ void pairs_release(aps_pairs *p) {
         if (pa->on_device)
             dfree(pa->block, pa->stream);
         else
-            cudaFreeHost(pa->block);
+            hfree(pa->block, pa->bytes);
         delete pa;
     }
     p->_priv = nullptr;
@@ -979,10 +979,11 @@ aps_status pairs_to_host(aps_pairs *p, cudaStream_t s) {
     pa->on_device = 0;
     pa->stream = s;
     const size_t n = (size_t)p->count;
-    cudaError_t e = cudaMallocHost(&pa->block, std::max<size_t>(n, 1) * 12);
-    if (e != cudaSuccess) {
+    pa->bytes = std::max<size_t>(n, 1) * 12;
+    aps_status hst = halloc(&pa->block, pa->bytes);
+    if (hst != APS_OK) {
         delete pa;
-        return cuda_status(e, "cudaMallocHost", __FILE__, __LINE__);
+        return hst;
     }
     char *blk = static_cast<char *>(pa->block);
     int32_t *hi = reinterpret_cast<int32_t *>(blk);
@@ -1184,7 +1185,10 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
     APS_TRY(ctr.alloc(16, s));
     APS_TRY(scratch.alloc((size_t)grid * NWARPS * JOIN_ECAP, s));
     APS_TRY(segs.alloc((size_t)nqw, s));
-    int64_t stage_cap = std::max<int64_t>({nq * 64, (int64_t)1 << 16});
+    // staging: the pairs per query this index's batches have needed so far (at least 64),
+    // plus one slab per group
+    const int64_t ppq16 = ix->q_ppq16.load(std::memory_order_relaxed);
+    int64_t stage_cap = std::max<int64_t>(nq * ppq16 / 16 + (int64_t)grid * G * 256, (int64_t)1 << 16);
     unsigned long long ch[16];
     for (int attempt = 0; attempt < 2; attempt++) {
         APS_TRY(stage.alloc((size_t)stage_cap, s));
@@ -1235,6 +1239,12 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
         APS_CUDA(cudaStreamSynchronize(s));
         if ((int64_t)ch[5] <= stage_cap) break;
         stage_cap = (int64_t)ch[5] + (int64_t)grid * G * 256;  // what was reserved, plus one slab per group
+    }
+    if (nq > 0) {  // remember what this batch needed (with a quarter more), for the next ones
+        const int64_t need16 = (int64_t)ch[5] * 20 / nq;
+        int64_t cur = ix->q_ppq16.load(std::memory_order_relaxed);
+        while (need16 > cur && !ix->q_ppq16.compare_exchange_weak(cur, need16, std::memory_order_relaxed)) {
+        }
     }
     if ((int64_t)ch[5] > stage_cap) {
         set_error("pair staging overflow persisted");

@@ -72,6 +72,53 @@ void dfree(void *p, cudaStream_t s) {
     if (p) cudaFreeAsync(p, s);
 }
 
+// ------------------------------------------------------------------ pinned host blocks
+static std::mutex g_host_mu;
+static std::vector<void *> g_host_free[64];  // cached blocks by size class (2^c bytes)
+static size_t g_host_cached = 0;
+constexpr size_t HOST_CACHE_MAX = (size_t)8 << 30;
+
+static int host_class(size_t bytes) {
+    int c = 20;  // 1 MiB
+    while (c < 63 && ((size_t)1 << c) < bytes) c++;
+    return c;
+}
+
+aps_status halloc(void **p, size_t bytes) {
+    *p = nullptr;
+    const int c = host_class(bytes);
+    {
+        std::lock_guard<std::mutex> lk(g_host_mu);
+        if (!g_host_free[c].empty()) {
+            *p = g_host_free[c].back();
+            g_host_free[c].pop_back();
+            g_host_cached -= (size_t)1 << c;
+            return APS_OK;
+        }
+    }
+    cudaError_t e = cudaMallocHost(p, (size_t)1 << c);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return cuda_status(e, "cudaMallocHost", __FILE__, __LINE__);
+    }
+    return APS_OK;
+}
+
+void hfree(void *p, size_t bytes) {
+    if (!p) return;
+    const int c = host_class(bytes);
+    {
+        std::lock_guard<std::mutex> lk(g_host_mu);
+        if (g_host_cached + ((size_t)1 << c) <= HOST_CACHE_MAX) {
+            g_host_free[c].push_back(p);
+            g_host_cached += (size_t)1 << c;
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
+
 // ------------------------------------------------------------------ prefix sum
 namespace {
 

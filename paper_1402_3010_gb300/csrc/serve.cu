@@ -8,6 +8,7 @@
 // nothing else runs). Every slot is a host thread with its own CUDA stream, so batches
 // admitted while others run overlap on the device; results are copied to pinned host
 // memory before the request is marked done.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -71,7 +72,7 @@ aps_status query_on_stream(aps_index *ix, const int64_t *qptr, const int32_t *qi
         vv = dv.p;
     }
     QueryArrays qa;
-    APS_TRY(prepare_queries(ix, p, ii, vv, nq, t, flags, s, qa));
+    APS_TRY(prepare_queries(ix, p, ii, vv, nq, t, flags, s, qa, (flags & APS_DEVICE_PTRS) ? -1 : qptr[nq]));
     aps_stats local{};
     APS_TRY(join_queries(ix, qa, t, flags, s, out, &local));
     if (stats) *stats = local;
@@ -128,6 +129,11 @@ struct aps_server {
     uint64_t next_ticket = 1;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
+    // device time line: every batch's device work lies between two events on its slot's
+    // stream, read against one reference event recorded when the server was created
+    cudaEvent_t ref = nullptr;
+    std::vector<cudaEvent_t> ev_begin, ev_end;       // per slot
+    std::vector<std::pair<float, float>> intervals;  // per completed batch: [begin, end) ms
 };
 
 namespace {
@@ -163,10 +169,19 @@ void worker(aps_server *sv, int slot) {
         r->t_start = now_s();
         lk.unlock();
         aps_pairs out{};
+        cudaStream_t s = sv->streams[slot];
+        const bool timed = cudaEventRecord(sv->ev_begin[slot], s) == cudaSuccess;
         aps_status st = query_on_stream(sv->ix, r->qptr.data(), r->qidx.data(), r->qval.data(), r->nq, r->t,
-                                        APS_HOST_OUTPUT, sv->streams[slot], &out, nullptr);
+                                        APS_HOST_OUTPUT, s, &out, nullptr);
         std::string msg = st == APS_OK ? std::string() : std::string(aps_last_error());
+        float b_ms = 0.f, e_ms = 0.f;
+        const bool have_iv = timed && st == APS_OK && cudaEventRecord(sv->ev_end[slot], s) == cudaSuccess &&
+                             cudaEventSynchronize(sv->ev_end[slot]) == cudaSuccess &&
+                             cudaEventElapsedTime(&b_ms, sv->ref, sv->ev_begin[slot]) == cudaSuccess &&
+                             cudaEventElapsedTime(&e_ms, sv->ref, sv->ev_end[slot]) == cudaSuccess;
+        if (!have_iv) cudaGetLastError();
         lk.lock();
+        if (have_iv) sv->intervals.emplace_back(b_ms, e_ms);
         r->status = st;
         r->err = msg;
         r->result = out;
@@ -218,8 +233,67 @@ aps_status aps_server_create(aps_index *index, size_t mem_budget, int32_t slots,
         }
         sv->streams.push_back(st);
     }
+    cudaError_t e = cudaEventCreate(&sv->ref);
+    for (int i = 0; i < slots && e == cudaSuccess; i++) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        e = cudaEventCreate(&a);
+        if (e == cudaSuccess) e = cudaEventCreate(&b);
+        sv->ev_begin.push_back(a);
+        sv->ev_end.push_back(b);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(sv->ref, sv->streams[0]);
+    if (e == cudaSuccess) e = cudaEventSynchronize(sv->ref);
+    if (e != cudaSuccess) {
+        for (cudaEvent_t x : sv->ev_begin) if (x) cudaEventDestroy(x);
+        for (cudaEvent_t x : sv->ev_end) if (x) cudaEventDestroy(x);
+        if (sv->ref) cudaEventDestroy(sv->ref);
+        for (cudaStream_t s2 : sv->streams) cudaStreamDestroy(s2);
+        delete sv;
+        return cuda_status(e, "server events", __FILE__, __LINE__);
+    }
     for (int i = 0; i < slots; i++) sv->workers.emplace_back(worker, sv, i);
     *out = sv;
+    return APS_OK;
+}
+
+aps_status aps_server_timeline(aps_server *sv, aps_timeline *out) {
+    if (!sv || !out) {
+        set_error("server and out must not be NULL");
+        return APS_EINVAL;
+    }
+    std::vector<std::pair<float, int>> ev;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (const auto &iv : sv->intervals) {
+            ev.emplace_back(iv.first, +1);
+            ev.emplace_back(iv.second, -1);
+        }
+        out->batches = (int64_t)sv->intervals.size();
+    }
+    // sweep the batches' [begin, end) intervals: time with >= 1 and >= 2 batches on the device
+    std::sort(ev.begin(), ev.end(), [](const std::pair<float, int> &a, const std::pair<float, int> &b) {
+        return a.first < b.first || (a.first == b.first && a.second < b.second);
+    });
+    double busy = 0, overlap = 0, span_lo = 0, span_hi = 0;
+    int cur = 0, most = 0;
+    for (size_t k = 0; k < ev.size(); k++) {
+        if (k > 0) {
+            const double dt = (double)ev[k].first - (double)ev[k - 1].first;
+            if (cur >= 1) busy += dt;
+            if (cur >= 2) overlap += dt;
+        }
+        cur += ev[k].second;
+        most = std::max(most, cur);
+    }
+    if (!ev.empty()) {
+        span_lo = ev.front().first;
+        span_hi = ev.back().first;
+    }
+    out->busy_ms = busy;
+    out->overlap_ms = overlap;
+    out->span_ms = span_hi - span_lo;
+    out->max_in_flight = most;
+    out->_reserved = 0;
     return APS_OK;
 }
 
@@ -326,6 +400,9 @@ void aps_server_free(aps_server *sv) {
         delete kv.second;
     }
     for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
+    for (cudaEvent_t x : sv->ev_begin) cudaEventDestroy(x);
+    for (cudaEvent_t x : sv->ev_end) cudaEventDestroy(x);
+    if (sv->ref) cudaEventDestroy(sv->ref);
     delete sv;
 }
 

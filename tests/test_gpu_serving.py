@@ -139,6 +139,11 @@ def test_serving_results_alone_equal_results_in_the_mix(aps):
                             mixed[k] = A.pairs_to_numpy(p)
                             A.aps_pairs_free(p)
             assert all(m is not None for m in mixed)
+            # the batches ran side by side on the device, not one after another
+            st = A.aps_server_timeline(sv)
+            assert st["batches"] == len(bounds)
+            assert st["max_in_flight"] >= 2 and st["overlap_ms"] > 0.0
+            assert 0.0 < st["busy_ms"] <= st["span_ms"] + 1e-3
         finally:
             A.aps_server_free(sv)
     finally:
