@@ -39,55 +39,73 @@ __global__ void k_vinst(const InstDesc *inst, int k, int64_t N, int32_t *vinst) 
 // Validation codes reported as (row << 8 | code) through atomicMin.
 enum { E_PTR = 1, E_IDX_RANGE = 2, E_IDX_ORDER = 3, E_VALUE = 4, E_NORM = 5 };
 
-// One thread per row: checks the row, records |x| and maxweight(x), and copies the values
-// (scaled to unit norm with APS_NORMALIZE).
+// One warp per row: checks the row, records |x| and maxweight(x), and copies the values
+// (scaled to unit norm with APS_NORMALIZE). The lanes read 32 components at a time; the
+// error code is that of the row's first bad component (range before order before value,
+// as for a sequential check). The float64 sum of squares is a warp tree sum.
 __global__ void k_validate(const int64_t *__restrict__ indptr, const int32_t *__restrict__ idx,
                            const float *__restrict__ val, const int32_t *__restrict__ vinst,
                            const InstDesc *__restrict__ inst, int64_t N, int64_t nnz, uint32_t flags,
                            int32_t *__restrict__ erow, float *__restrict__ vout, int32_t *__restrict__ len,
                            float *__restrict__ mw, unsigned long long *err) {
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += (int64_t)gridDim.x * blockDim.x) {
-        int64_t a = indptr[x], b = indptr[x + 1];
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < N; x += nwarps) {
+        const int64_t a = indptr[x], b = indptr[x + 1];
         if (a < 0 || b < a || b > nnz) {
-            atomicMin(err, ((unsigned long long)x << 8) | E_PTR);
-            len[x] = 0;
-            mw[x] = 0.f;
+            if (lane == 0) {
+                atomicMin(err, ((unsigned long long)x << 8) | E_PTR);
+                len[x] = 0;
+                mw[x] = 0.f;
+            }
             continue;
         }
-        int m = inst[vinst[x]].m;
-        int prev = -1;
-        int code = 0;
+        const int m = inst[vinst[x]].m;
+        int code = 0, prev_last = -1;
         double ss = 0.0;
-        for (int64_t p = a; p < b; p++) {
-            int d = idx[p];
-            float v = val[p];
-            if (d < 0 || d >= m) code = code ? code : E_IDX_RANGE;
-            else if (d <= prev) code = code ? code : E_IDX_ORDER;
-            if (!(v > 0.f) || !isfinite(v)) code = code ? code : E_VALUE;
-            prev = d;
-            ss += (double)v * (double)v;
-            erow[p] = (int32_t)x;
+        for (int64_t base = a; base < b; base += 32) {
+            const int64_t p = base + lane;
+            const int cnt = (int)min((int64_t)32, b - base);
+            int d = 0;
+            float v = 1.f;
+            if (p < b) {
+                d = idx[p];
+                v = val[p];
+                erow[p] = (int32_t)x;
+            }
+            int prevd = __shfl_up_sync(0xffffffffu, d, 1);
+            if (lane == 0) prevd = prev_last;
+            int ec = 0;
+            if (p < b) {
+                if (d < 0 || d >= m) ec = E_IDX_RANGE;
+                else if (d <= prevd) ec = E_IDX_ORDER;
+                else if (!(v > 0.f) || !isfinite(v)) ec = E_VALUE;
+            }
+            const unsigned bad = __ballot_sync(0xffffffffu, ec != 0);
+            if (!code && bad) code = __shfl_sync(0xffffffffu, ec, __ffs(bad) - 1);
+            if (p < b) ss += (double)v * (double)v;
+            prev_last = __shfl_sync(0xffffffffu, d, cnt - 1);
         }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         float best = 0.f;
         if (b > a && !code) {
-            double nrm = sqrt(ss);
-            if (flags & APS_NORMALIZE) {
-                for (int64_t p = a; p < b; p++) {
-                    float v = (float)((double)val[p] / nrm);
-                    vout[p] = v;
-                    best = fmaxf(best, v);
-                }
-            } else {
-                if ((flags & APS_SUBUNIT_NORMS) ? nrm > 1.0 + 1e-3 : fabs(nrm - 1.0) > 1e-3) code = E_NORM;
-                for (int64_t p = a; p < b; p++) {
-                    vout[p] = val[p];
-                    best = fmaxf(best, val[p]);
-                }
+            const double nrm = sqrt(ss);
+            if (!(flags & APS_NORMALIZE) && ((flags & APS_SUBUNIT_NORMS) ? nrm > 1.0 + 1e-3 : fabs(nrm - 1.0) > 1e-3))
+                code = E_NORM;
+            for (int64_t p = a + lane; p < b; p += 32) {
+                const float v = (flags & APS_NORMALIZE) ? (float)((double)val[p] / nrm) : val[p];
+                vout[p] = v;
+                best = fmaxf(best, v);
             }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
         }
-        if (code) atomicMin(err, ((unsigned long long)x << 8) | (unsigned long long)code);
-        len[x] = (int32_t)(b - a);
-        mw[x] = best;
+        if (lane == 0) {
+            if (code) atomicMin(err, ((unsigned long long)x << 8) | (unsigned long long)code);
+            len[x] = (int32_t)(b - a);
+            mw[x] = best;
+        }
     }
 }
 
@@ -150,57 +168,61 @@ __global__ void k_canon_gather(const uint64_t *__restrict__ keys, const uint32_t
 // x[i] * maxweight_i(V) in float64; qsplit = the first component where b >= t (the
 // remscore boundary for x as a query). The index split is qsplit, or 0 without partial
 // indexing, or, for a queryable index, the first component where ||x_prefix||_2 reaches
-// t (with a margin for the 1e-3 norm tolerance).
+// t (with a margin for the 1e-3 norm tolerance). One warp per row: the lanes load 32
+// components and form their products (exact in float64) side by side; the running sums
+// add them left to right, each term broadcast to every lane, so b is bit-identical to a
+// sequential sum in component order.
 __global__ void k_split(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
                         const float *__restrict__ cval, const float *__restrict__ mwr,
                         const int32_t *__restrict__ vinst, const InstDesc *__restrict__ inst, int64_t N,
                         uint32_t flags, int32_t *split, int32_t *qsplit, float *mwpre, float *pnorm) {
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += (int64_t)gridDim.x * blockDim.x) {
-        const InstDesc I = inst[vinst[x]];
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < N; x += nwarps) {
+        const InstDesc &I = inst[vinst[x]];
         const double t = (double)I.t;
-        int64_t a = cptr[x], b = cptr[x + 1];
-        int32_t L = (int32_t)(b - a);
+        const int64_t a = cptr[x], b = cptr[x + 1];
+        const int32_t L = (int32_t)(b - a);
+        const bool need_cs = (flags & APS_QUERYABLE) != 0;  // the norm-bound split only for queryable indexes
         int32_t qs = L, cs = L;
         double bmw = 0.0, ss = 0.0;
-        // four components' loads at a time; the sums still run in component order
-        bool stop = false;
-        for (int64_t p0 = a; p0 < b && !stop; p0 += 4) {
-            double v4[4], m4[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int64_t p = min(p0 + u, b - 1);
-                v4[u] = (double)cval[p];
-                m4[u] = (double)mwr[(int64_t)I.rbase + crank[p]];
+        for (int64_t base = a; base < b && (qs == L || (need_cs && cs == L)); base += 32) {
+            const int64_t p = base + lane;
+            const int cnt = (int)min((int64_t)32, b - base);
+            double pr = 0.0, sq = 0.0;
+            if (p < b) {
+                const double v = (double)cval[p];
+                pr = v * (double)mwr[(int64_t)I.rbase + crank[p]];
+                sq = v * v;
             }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int64_t p = p0 + u;
-                if (stop || p >= b) continue;
-                bmw += v4[u] * m4[u];
-                ss += v4[u] * v4[u];
-                if (qs == L && bmw >= t) qs = (int32_t)(p - a);
-                if (cs == L && ss * (1.0 + 2e-3) >= t * t) cs = (int32_t)(p - a);
-                if (qs < L && cs < L) stop = true;
+            for (int j = 0; j < cnt; j++) {
+                bmw += __shfl_sync(0xffffffffu, pr, j);
+                if (qs == L && bmw >= t) qs = (int32_t)(base - a) + j;
+                if (need_cs) {
+                    ss += __shfl_sync(0xffffffffu, sq, j);
+                    if (cs == L && ss * (1.0 + 2e-3) >= t * t) cs = (int32_t)(base - a) + j;
+                }
             }
         }
-        int32_t sp = (flags & APS_NO_PARTIAL_INDEX) ? 0 : ((flags & APS_QUERYABLE) ? cs : qs);
+        const int32_t sp = (flags & APS_NO_PARTIAL_INDEX) ? 0 : ((flags & APS_QUERYABLE) ? cs : qs);
         float best = 0.f;
         double pss = 0.0;
-        for (int64_t p0 = a; p0 < a + sp; p0 += 4) {
-            float c4[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) c4[u] = cval[min(p0 + u, a + sp - 1)];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                if (p0 + u >= a + sp) continue;
-                best = fmaxf(best, c4[u]);
-                pss += (double)c4[u] * (double)c4[u];
-            }
+        for (int64_t p = a + lane; p < a + sp; p += 32) {
+            const float c = cval[p];
+            best = fmaxf(best, c);
+            pss += (double)c * (double)c;
         }
-        split[x] = sp;
-        qsplit[x] = qs;
-        mwpre[x] = best;
-        pnorm[x] = sp ? __double2float_ru(sqrt(pss) * (1.0 + 1.1e-3)) : 0.f;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+            pss += __shfl_xor_sync(0xffffffffu, pss, o);
+        }
+        if (lane == 0) {
+            split[x] = sp;
+            qsplit[x] = qs;
+            mwpre[x] = best;
+            pnorm[x] = sp ? __double2float_ru(sqrt(pss) * (1.0 + 1.1e-3)) : 0.f;
+        }
     }
 }
 
@@ -443,8 +465,8 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     // ---- a1: validation, |x|, maxweight(x), per-dimension statistics
     k_vinst<<<gN, T256, 0, s>>>(d.inst.p, k, N, d.vinst.p);
     APS_LAUNCH_CHECK();
-    k_validate<<<gN, T256, 0, s>>>(indptr, idx, val, d.vinst.p, d.inst.p, N, nnz, ix->flags, erow.p, vout.p,
-                                   d.len.p, d.mw.p, err.p);
+    k_validate<<<grid_for(N * 32, T256), T256, 0, s>>>(indptr, idx, val, d.vinst.p, d.inst.p, N, nnz, ix->flags,
+                                                       erow.p, vout.p, d.len.p, d.mw.p, err.p);
     APS_LAUNCH_CHECK();
     unsigned long long e_h = ~0ull;
     APS_CUDA(cudaMemcpyAsync(&e_h, err.p, sizeof(e_h), cudaMemcpyDeviceToHost, s));
@@ -497,8 +519,8 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     }
     // ---- a3: partial-indexing split
     APS_TRY(d.pnorm.alloc((size_t)std::max<int64_t>(N, 1), s));
-    k_split<<<gN, T256, 0, s>>>(d.cptr.p, d.crank.p, d.cval.p, d.mwr.p, d.vinst.p, d.inst.p, N, ix->flags,
-                                d.split.p, d.qsplit.p, d.mwpre.p, d.pnorm.p);
+    k_split<<<grid_for(N * 32, T256), T256, 0, s>>>(d.cptr.p, d.crank.p, d.cval.p, d.mwr.p, d.vinst.p, d.inst.p, N,
+                                                    ix->flags, d.split.p, d.qsplit.p, d.mwpre.p, d.pnorm.p);
     APS_LAUNCH_CHECK();
     // ---- a4: suffix inverted index
     {
@@ -648,8 +670,8 @@ aps_status prepare_queries(const aps_index *ix, const int64_t *qptr, const int32
     APS_TRY(err.alloc(1, s));
     APS_CUDA(cudaMemsetAsync(err.p, 0xff, sizeof(unsigned long long), s));
     if (nq > 0) {
-        k_validate<<<grid_for(nq, T256), T256, 0, s>>>(qptr, qidx, qval, vinst.p, dinst.p, nq, nnz, flags, erow.p,
-                                                       vout.p, len.p, qa.mw.p, err.p);
+        k_validate<<<grid_for((int64_t)nq * 32, T256), T256, 0, s>>>(qptr, qidx, qval, vinst.p, dinst.p, nq, nnz,
+                                                                     flags, erow.p, vout.p, len.p, qa.mw.p, err.p);
         APS_LAUNCH_CHECK();
     }
     unsigned long long e_h = ~0ull;
