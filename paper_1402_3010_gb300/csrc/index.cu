@@ -169,9 +169,21 @@ __global__ void k_canon_gather(const uint64_t *__restrict__ keys, const uint32_t
 // remscore boundary for x as a query). The index split is qsplit, or 0 without partial
 // indexing, or, for a queryable index, the first component where ||x_prefix||_2 reaches
 // t (with a margin for the 1e-3 norm tolerance). One warp per row: the lanes load 32
-// components and form their products (exact in float64) side by side; the running sums
-// add them left to right, each term broadcast to every lane, so b is bit-identical to a
-// sequential sum in component order.
+// components, form their products (exact in float64) and take the running sums by a warp
+// prefix scan, carried from one 32-component step to the next. The scan associates the
+// terms differently from a left-to-right sum, so where b comes within rounding of t the
+// split may fall one component apart from a sequential one; either is a valid split (the
+// bound of the unindexed prefix stays below t up to rounding, which the float64 band of
+// the decisions covers).
+__device__ __forceinline__ double warp_incl_scan_f64(double v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
 __global__ void k_split(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
                         const float *__restrict__ cval, const float *__restrict__ mwr,
                         const int32_t *__restrict__ vinst, const InstDesc *__restrict__ inst, int64_t N,
@@ -185,43 +197,46 @@ __global__ void k_split(const int64_t *__restrict__ cptr, const int32_t *__restr
         const int32_t L = (int32_t)(b - a);
         const bool need_cs = (flags & APS_QUERYABLE) != 0;  // the norm-bound split only for queryable indexes
         int32_t qs = L, cs = L;
-        double bmw = 0.0, ss = 0.0;
+        double bmw = 0.0, ss = 0.0;  // sums of the components before this step
         for (int64_t base = a; base < b && (qs == L || (need_cs && cs == L)); base += 32) {
             const int64_t p = base + lane;
-            const int cnt = (int)min((int64_t)32, b - base);
             double pr = 0.0, sq = 0.0;
             if (p < b) {
                 const double v = (double)cval[p];
                 pr = v * (double)mwr[(int64_t)I.rbase + crank[p]];
                 sq = v * v;
             }
-            for (int j = 0; j < cnt; j++) {
-                bmw += __shfl_sync(0xffffffffu, pr, j);
-                if (qs == L && bmw >= t) qs = (int32_t)(base - a) + j;
-                if (need_cs) {
-                    ss += __shfl_sync(0xffffffffu, sq, j);
-                    if (cs == L && ss * (1.0 + 2e-3) >= t * t) cs = (int32_t)(base - a) + j;
-                }
+            const double bi = bmw + warp_incl_scan_f64(pr, lane);
+            const unsigned hit = __ballot_sync(0xffffffffu, p < b && bi >= t);
+            if (qs == L && hit) qs = (int32_t)(base - a) + __ffs(hit) - 1;
+            bmw = __shfl_sync(0xffffffffu, bi, 31);
+            if (need_cs) {
+                const double si = ss + warp_incl_scan_f64(sq, lane);
+                const unsigned hc = __ballot_sync(0xffffffffu, p < b && si * (1.0 + 2e-3) >= t * t);
+                if (cs == L && hc) cs = (int32_t)(base - a) + __ffs(hc) - 1;
+                ss = __shfl_sync(0xffffffffu, si, 31);
             }
         }
         const int32_t sp = (flags & APS_NO_PARTIAL_INDEX) ? 0 : ((flags & APS_QUERYABLE) ? cs : qs);
-        float best = 0.f;
-        double pss = 0.0;
+        // maxweight(x') and an upper bound of ||x'||_2 (float32 with every operation rounded
+        // up, so the bound can only come out above the exact norm; times 1 + 1.1e-3 for the
+        // 1e-3 norm tolerance of the vectors it will be dotted with)
+        float best = 0.f, pss = 0.f;
         for (int64_t p = a + lane; p < a + sp; p += 32) {
             const float c = cval[p];
             best = fmaxf(best, c);
-            pss += (double)c * (double)c;
+            pss = __fmaf_ru(c, c, pss);
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-            pss += __shfl_xor_sync(0xffffffffu, pss, o);
+            pss = __fadd_ru(pss, __shfl_xor_sync(0xffffffffu, pss, o));
         }
         if (lane == 0) {
             split[x] = sp;
             qsplit[x] = qs;
             mwpre[x] = best;
-            pnorm[x] = sp ? __double2float_ru(sqrt(pss) * (1.0 + 1.1e-3)) : 0.f;
+            pnorm[x] = sp ? __fmul_ru(__fsqrt_ru(pss), 1.0011f) : 0.f;
         }
     }
 }
@@ -233,13 +248,22 @@ __global__ void k_post_keys(const int64_t *__restrict__ cptr, const int32_t *__r
                             const int32_t *__restrict__ erow, const int32_t *__restrict__ split,
                             const int32_t *__restrict__ vinst, const InstDesc *__restrict__ inst, int64_t nnz,
                             int64_t M, uint64_t *keys, uint32_t *vals, unsigned long long *nsuf) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
-        int64_t x = erow[p];
-        const InstDesc &I = inst[vinst[x]];
-        bool suf = (p - cptr[x]) >= split[x];
-        if (suf) atomicAdd(nsuf, 1ull);
-        keys[p] = suf ? (uint64_t)I.rbase + (uint64_t)crank[p] : (uint64_t)M;
-        vals[p] = (uint32_t)p;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of 32: warps stay whole
+    // the loop runs while the warp's first entry is in range, so the count below is taken
+    // by whole warps (one atomic per warp instead of one per entry)
+    for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; p0 < nnz; p0 += stride) {
+        const int64_t p = p0 + lane;
+        bool suf = false;
+        if (p < nnz) {
+            const int64_t x = erow[p];
+            const InstDesc &I = inst[vinst[x]];
+            suf = (p - cptr[x]) >= split[x];
+            keys[p] = suf ? (uint64_t)I.rbase + (uint64_t)crank[p] : (uint64_t)M;
+            vals[p] = (uint32_t)p;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, suf);
+        if (lane == 0 && bal) atomicAdd(nsuf, (unsigned long long)__popc(bal));
     }
 }
 

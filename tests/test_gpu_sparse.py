@@ -292,9 +292,28 @@ def test_injected_allocation_failure_then_recovery(aps):
 # ------------------------------------------------------------------- index steps
 
 
+def _split_is_valid(cv, mwr, cr, a, b, k, t):
+    """Partial indexing at k: the bound sum x[i]*maxweight_i(V) of the first k components
+    stays below t and the next component brings it to t (exact rationals; 1e-12 slack for
+    the float64 rounding of the running bound)."""
+    from fractions import Fraction
+
+    bound = Fraction(0)
+    for p in range(a, a + k):
+        bound += Fraction(float(cv[p])) * Fraction(float(mwr[cr[p]]))
+    ok = bound < Fraction(t) or abs(float(bound) - t) < 1e-12
+    if a + k < b:
+        nxt = bound + Fraction(float(cv[a + k])) * Fraction(float(mwr[cr[a + k]]))
+        ok = ok and (nxt >= Fraction(t) or abs(float(nxt) - t) < 1e-12)
+    return ok
+
+
 def test_index_build_steps_match_oracle(aps):
     """a1 statistics, a2 ranks and rank-ordered rows, a3 partial-indexing split and a4
-    posting lists, each against the oracle's step (bit-exact)."""
+    posting lists, each against the oracle's step: bit-exact, except that the split (whose
+    float64 running bound the GPU sums in another association order) may fall elsewhere
+    where the bound comes within rounding of t; there it is checked for validity and
+    maximality in exact arithmetic."""
     import paper_1402_3010_gb300 as A
 
     c = pl_small(61, n=4000, m=3000)
@@ -313,8 +332,16 @@ def test_index_build_steps_match_oracle(aps):
     assert np.array_equal(ex["rank_of_dim"], aux["rank"])
     assert np.array_equal(ex["crank"], aux["crank"])
     assert np.array_equal(ex["cval"], aux["cval"])
-    assert np.array_equal(ex["split"], split)
-    assert np.array_equal(ex["qsplit"], split)
+    assert np.array_equal(ex["qsplit"], ex["split"])
+    differ = np.nonzero(ex["split"] != split)[0]
+    assert differ.size <= max(2, c.n // 1000)
+    mwr = aux["mwr"]
+    for x in differ.tolist():
+        a, b = int(c.indptr[x]), int(c.indptr[x + 1])
+        assert _split_is_valid(aux["cval"], mwr, aux["crank"], a, b, int(ex["split"][x]), f32(t))
+    split = ex["split"]
+    mwp = np.array([aux["cval"][c.indptr[x]:c.indptr[x] + split[x]].max() if split[x] else 0.0 for x in range(c.n)],
+                   np.float32)
     assert np.array_equal(ex["mw_pre"], mwp)
     # posting lists: per rank, the multiset of (vector, weight) of the indexed suffixes
     rows = np.repeat(np.arange(c.n), np.diff(c.indptr))
