@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched workload: time the default tile table instead of the autotuned one")
     ap.add_argument("--workload", default="sparse",
-                    choices=["sparse", "dense", "batched", "serving", "ablation", "graph", "horizontal", "vertical"],
+                    choices=["sparse", "dense", "batched", "serving", "ablation", "graph", "horizontal", "vertical",
+                             "split"],
                     help="sparse: the 200k-vector sparse self-join (default line); dense: the 200k x 256 "
                          "embedding self-join on the tensor cores; batched: 512 independent sparse "
                          "instances; serving: query batches against a 1M-vector resident index")
@@ -991,7 +992,62 @@ def run_small(args):
     return line
 
 
-FORM_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "dtype", "config", "roofline", "latency_ms",
+def run_split(args):
+    """The vertical algorithm's local pruning inside the join (Sec. 5.1, Lemma 1) on the
+    200k-vector workload: the join of the plain kernel next to joins whose costliest
+    vectors run as dimension blocks on different CTAs (aps_all_pairs_split), with the pair
+    count of each (the tests check the pair sets against the oracle)."""
+    import torch
+
+    import paper_1402_3010_gb300 as aps
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    aps.load()
+    c = workload(args.n, args.m)
+    t = float(np.float32(args.t))
+    stream = torch.cuda.current_stream(dev)
+    ip, ix, vv = (torch.from_numpy(a).to(dev) for a in (c.indptr, c.idx, c.val))
+    h = aps.aps_build_index(ip, ix, vv, c.n, c.m, t, 0, stream)
+    steps = max(args.steps, 3)
+
+    def timed(fn):
+        fn()  # warm
+        join, call, pairs = [], [], 0
+        with no_gc():
+            for _ in range(steps):
+                t0 = time.perf_counter()
+                p = fn()
+                pairs = int(p.count)
+                aps.aps_pairs_free(p)
+                call.append(1e3 * (time.perf_counter() - t0))
+                join.append(aps.aps_index_stats(h)["ms_join"])
+        return statistics.mean(join), statistics.mean(call), pairs
+
+    clocks = Clocks(0)
+    clocks.start()
+    pj, pc, pp = timed(lambda: aps.aps_all_pairs(h))
+    rows = []
+    for nblk, heavy in ((2, 200), (4, 200), (2, 2000), (4, 2000)):
+        j, cl, pr = timed(lambda: aps.aps_all_pairs_split(h, nblk, heavy))
+        rows.append({"blocks": nblk, "heavy_vectors": heavy, "join_kernel_ms": round(j, 3), "call_ms": round(cl, 3),
+                     "pairs": pr, "same_count_as_plain": pr == pp})
+    clk = clocks.stop()
+    aps.aps_index_free(h)
+    evals = c.n * (c.n - 1) // 2
+    return {
+        "metric": METRIC, "value": evals / (pc * 1e-3), "unit": UNIT, "ms_per_step": pc, "steps": steps,
+        "dtype": "f32",
+        "config": {"workload": "the vertical algorithm's local pruning inside the join, on " + WORKLOAD,
+                   "n": c.n, "m": c.m, "t": t, "step": "one join call of the built index"},
+        "split": {"plain_join_kernel_ms": round(pj, 3), "plain_call_ms": round(pc, 3), "plain_pairs": pp,
+                  "runs": rows,
+                  "note": "call_ms includes the merge of the blocks' pairs (sort, first occurrences, placement)"},
+        "clocks": clk,
+    }
+
+
+FORM_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "dtype", "config", "roofline", "latency_ms", "split",
              "phases_ms", "work", "serving", "tiles", "clocks", "cpu_baseline", "accuracy", "precision_vs_fp64",
              "e2e", "gpu_launches", "gpu_launches_unit")
 
@@ -1009,7 +1065,8 @@ def run_forms(args):
     a.steps, a.warmup, a.e2e_steps = args.form_steps, 3, 2
     forms = {}
     for name, fn in (("small", lambda: run_small(a)), ("dense", lambda: run_dense(a, 0, 1)),
-                     ("batched", lambda: run_batched(a)), ("serving", lambda: run_serving(a))):
+                     ("batched", lambda: run_batched(a)), ("serving", lambda: run_serving(a)),
+                     ("split", lambda: run_split(a))):
         t0 = time.perf_counter()
         rec = as_form(fn())
         rec["seconds"] = round(time.perf_counter() - t0, 1)
@@ -1402,6 +1459,8 @@ def main():
         line = run_horizontal(args, rank, world)
     elif args.workload == "vertical":
         line = run_vertical(args, rank, world)
+    elif args.workload == "split":
+        line = run_split(args)
     else:
         line = run_aps(args, rank, world)
         if line is not None and world == 1 and not args.no_forms and args.workload == "sparse":

@@ -146,6 +146,22 @@ aps_status aps_build_index(const int64_t *indptr, const int32_t *idx, const floa
  * APS_EOVERFLOW (the staging still overflowed after growing twice); *out is then empty. */
 aps_status aps_all_pairs(aps_index *index, uint32_t flags, aps_pairs *out);
 
+/* The self-join of aps_all_pairs with the vertical algorithm's local pruning inside the
+ * join (Sec. 5.1: Par-All-Pairs-0-Vert, Lemma 1, local threshold t/p). The `heavy`
+ * costliest vectors of the index (the front of its cost-ordered work list; all of them when
+ * heavy exceeds the count) are each joined as nblk dimension blocks, on different CTAs: a
+ * block walks every nblk-th of the vector's creating components (those remscore lets
+ * create candidates) and all of its updating ones. A match scores A + dot(x, y') >= t and
+ * the blocks that created y hold all of A between them, so one block has A_b >=
+ * (t - ||y'||_2) / nblk; a block keeps y only then (local pruning), decides the kept
+ * candidates by their float64 dot product over all of y, and the blocks' pairs are merged
+ * (sorted, duplicates dropped) into the vectors' output runs. The result equals
+ * aps_all_pairs' (i < j, sorted by (i, j)); only the work distribution differs.
+ * 2 <= nblk <= 8, heavy >= 0 (0: the plain join). Errors: APS_EINVAL (NULL arguments, a
+ * batched index, nblk or heavy out of range), APS_ENOMEM, APS_ECUDA, APS_EOVERFLOW. */
+aps_status aps_all_pairs_split(aps_index *index, int32_t nblk, int64_t heavy, uint32_t flags,
+                               aps_pairs *out);
+
 /* Match nq external query vectors (CSR as in aps_build_index) against the index
  * (the local matching step of the horizontal algorithm, Alg. 6): every (q, y) with
  * dot(q, y) >= t, as i = query row, j = vector id, sorted by (i, j). The index must

@@ -146,6 +146,7 @@ def load():
         sigs = {
             "aps_build_index": (_i32, [_P, _P, _P, _i32, _i32, _f32, _u32, _P, ctypes.POINTER(_P)]),
             "aps_all_pairs": (_i32, [_P, _u32, ctypes.POINTER(aps_pairs)]),
+            "aps_all_pairs_split": (_i32, [_P, _i32, _i64, _u32, ctypes.POINTER(aps_pairs)]),
             "aps_query": (_i32, [_P, _P, _P, _P, _i32, _f32, _u32, ctypes.POINTER(aps_pairs)]),
             "aps_index_export": (_i32, [_P] + [_P] * 13),
             "aps_index_info": (_i32, [_P, _P, _P, _P, _P]),
@@ -274,6 +275,17 @@ def aps_all_pairs(index: int, flags: int = 0) -> aps_pairs:
     lib = load()
     out = aps_pairs()
     _check(lib.aps_all_pairs(index, int(flags), ctypes.byref(out)), "aps_all_pairs")
+    return out
+
+
+def aps_all_pairs_split(index: int, nblk: int, heavy: int, flags: int = 0) -> aps_pairs:
+    """The self-join with the `heavy` costliest vectors joined as nblk dimension blocks
+    each (the vertical algorithm's local pruning inside the join); same pairs as
+    aps_all_pairs."""
+    lib = load()
+    out = aps_pairs()
+    _check(lib.aps_all_pairs_split(index, int(nblk), int(heavy), int(flags), ctypes.byref(out)),
+           "aps_all_pairs_split")
     return out
 
 

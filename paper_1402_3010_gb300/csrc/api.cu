@@ -162,6 +162,37 @@ aps_status aps_all_pairs(aps_index *index, uint32_t flags, aps_pairs *out) {
     return st;
 }
 
+aps_status aps_all_pairs_split(aps_index *index, int32_t nblk, int64_t heavy, uint32_t flags, aps_pairs *out) {
+    if (!index || !out) {
+        set_error("index and out must not be NULL");
+        return APS_EINVAL;
+    }
+    memset(out, 0, sizeof(*out));
+    if (index->k != 1) {
+        set_error("aps_all_pairs_split needs a single-instance index");
+        return APS_EINVAL;
+    }
+    if (nblk < 2 || nblk > 8 || heavy < 0) {
+        set_error("need 2 <= nblk <= 8 dimension blocks and heavy >= 0");
+        return APS_EINVAL;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, index->stream);
+    aps_status st = join_all_pairs(index, flags, out, nullptr, nblk, heavy);
+    if (st == APS_OK && (flags & APS_HOST_OUTPUT)) st = pairs_to_host(out, index->stream);
+    cudaEventRecord(e1, index->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    index->stats.ms_total = ms;
+    if (st != APS_OK) pairs_release(out);
+    return st;
+}
+
 aps_status aps_index_export(const aps_index *ix, int32_t *len, float *mw, int32_t *nnz_d, float *mw_d,
                             int32_t *rank_of_dim, int32_t *crank, float *cval, int32_t *split, int32_t *qsplit,
                             float *mw_pre, int64_t *list_ptr, int32_t *post_id, float *post_w) {

@@ -192,8 +192,10 @@ aps_status autotune_batch(int32_t k, const int64_t *ro, const int64_t *hptr, con
 
 // Self-join of every instance of the index; fills a device aps_pairs (i, j, score)
 // with per-instance ranges in pair_offsets_h (k+1 entries, may be null).
+// nblk >= 2 and heavy > 0 (single-instance indexes): the vertical split with local pruning
+// for the `heavy` costliest vectors, joined as nblk dimension blocks each (Sec. 5.1, Lemma 1).
 aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out,
-                          std::vector<int64_t> *pair_offsets_h);
+                          std::vector<int64_t> *pair_offsets_h, int nblk = 0, int64_t heavy = 0);
 
 // The self-join of a single-instance index with every buffer carved out of `arena`
 // (arena_bytes, 256-byte aligned) and at most max_ctas CTAs; pairs land in the caller's

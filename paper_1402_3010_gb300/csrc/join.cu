@@ -53,6 +53,14 @@ struct JoinParams {
     const int4 *vmeta;   // {row offset, |x|, |x'|, maxweight(x')}
     const int4 *vcand;   // {row offset, |y'|, maxweight(y'), ||y'||_2 bound}
     const uint32_t *pn4; // 4-bit ||y'||_2 codes, eight per word (instance I from word I.pbase)
+    // dimension-block items (the vertical split with local pruning, Sec. 5.1): iblk[it] >= 0
+    // makes work item it one of nblk blocks of the vector items[it]; null: none
+    const int8_t *iblk;
+    int nblk;
+    unsigned long long *sp_key;    // pairs found by block items: local x * n + local y
+    uint32_t *sp_score;            // their float32 scores (bits)
+    unsigned long long *sp_count;  // pairs reserved in sp_key / sp_score
+    int64_t sp_cap;
     const int32_t *qsplit;
     const float *mw;
     const int64_t *lptr;
@@ -267,9 +275,10 @@ __device__ __forceinline__ float dot_prefix(const int2 *__restrict__ yr, int ys,
     return acc;
 }
 
-// QMODE: external queries against the index (P.qmode = 1); compiled separately so that
-// the self-join carries none of the query path's state.
-template <bool QMODE>
+// QMODE: external queries against the index (P.qmode = 1); SPLIT: a self-join whose work
+// list may hold dimension-block items (P.iblk). Each is compiled separately, so that the
+// plain self-join carries none of the other paths' state.
+template <bool QMODE, bool SPLIT = false>
 __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const bool f_minsize = !(P.flags & APS_NO_MINSIZE);
@@ -319,6 +328,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
         // query mode: item = (query, window), so the windows of a long query run on several
         // CTAs at once instead of one after another
         const int64_t x = QMODE ? it / P.qnw : (int64_t)P.items[it];
+        const int blk = (SPLIT && P.iblk) ? (int)P.iblk[it] : -1;  // group-uniform
         const int wq_item = QMODE ? (int)(it % P.qnw) : 0;
         const InstDesc I = P.inst[QMODE ? 0 : P.vinst[x]];
         const int32_t lx = QMODE ? -1 : (int32_t)(x - I.vbase);
@@ -331,6 +341,13 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
         const float beta = fmaxf(1e-5f, (float)(xl + 2) * 1.1920929e-7f);  // (|x|+2) * 2^-23
         // no component reaches remscore >= t: x can create no candidate at all
         if (f_remscore ? qs >= xl : xl == 0) continue;
+        // A block item walks its share of x's creating components (every nblk-th, from its
+        // block index on) and all of x's updating ones, which only add to candidates its
+        // own creating components made.
+        const int cstr = blk < 0 ? 1 : P.nblk, coff = blk < 0 ? 0 : blk;
+        const int ncreate = blk < 0 ? xl - qs : (xl - qs > blk ? (xl - qs - blk + P.nblk - 1) / P.nblk : 0);
+        const int nwalk = ncreate + qs;  // components this item walks
+        if (ncreate == 0) continue;
         // minsize: a match y needs |y| >= t / maxweight(x) (margin for rounding and the
         // 1e-3 norm tolerance); the size class byte of each entry is compared with it
         // (float, directed rounding: numerator down, denominator up, quotient down, so the
@@ -340,7 +357,6 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
             smin = (int)ceilf(fminf(__fdiv_rd(__fsub_rd(t, beta), __fmul_ru(mwx, 1.0020001f)), 255.f));
         const uint32_t smin_tag = (uint32_t)max(smin, 0) << 24;
         const int32_t idmask = I.packed ? 0x00ffffff : 0x7fffffff;
-        const int ncreate = xl - qs;  // components walked first; they may create candidates
         // dense table of x over small ranks for dot(x, y')
         for (int i = gt; i < RG; i += GT) xtab[i] = 0.f;
         gsync(G, g, GT);
@@ -359,21 +375,21 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
             const int wn = min(I.W, I.n - w0);
             const int lo = max(0, lx + 1 - w0);
             bool created = false;  // any entry of a creating component in this window
-            if (f_upper) {  // the window's 4-bit ||y'||_2 codes into shared memory, behind the accumulation
+            if (f_upper || blk >= 0) {  // the window's 4-bit ||y'||_2 codes into shared memory, behind the accumulation
                 const uint32_t *src = P.pn4 + I.pbase + (w0 >> 3);
                 for (int q = gt; q < (wn + 31) >> 5; q += GT) cp_async16(pn4s + 4 * q, src + 4 * q);
                 cp_async_commit();
             }
             // ---------------- accumulate. Components are walked creating-first (those with
             // remscore >= t), so every batch holds its creating part before its updating part.
-            if (xl <= 32) {
+            if (nwalk <= 32) {
                 // a short x: every warp builds the window's segment table itself, lane c
                 // holding component c (no shared table, no barrier)
                 int64_t st = 0;
                 int cnt = 0;
                 float xv = 0.f;
-                if (lane < xl) {
-                    const int c = lane < ncreate ? qs + lane : lane - ncreate;
+                if (lane < nwalk) {
+                    const int c = lane < ncreate ? qs + coff + lane * cstr : lane - ncreate;
                     const int2 e = c < xs ? xr[c] : xrow[c];
                     const int64_t R = (int64_t)I.rbase + e.x;
                     xv = __int_as_float(e.y);
@@ -413,14 +429,14 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                 cp_async_wait_all();  // the window's codes have landed (visible after the barrier)
                 gsync(G, g, GT);
             } else
-            for (int c0 = 0; c0 < xl; c0 += GT) {
+            for (int c0 = 0; c0 < nwalk; c0 += GT) {
                 const int cp = c0 + gt;
                 int64_t st = 0;
                 int32_t cnt = 0;
                 float xv = 0.f;
                 const bool ph0 = cp < ncreate;
-                if (cp < xl) {
-                    const int c = ph0 ? qs + cp : cp - ncreate;
+                if (cp < nwalk) {
+                    const int c = ph0 ? qs + coff + cp * cstr : cp - ncreate;
                     const int2 e = c < xs ? xr[c] : xrow[c];  // x's row from shared memory when held there
                     const int64_t R = (int64_t)I.rbase + e.x;
                     xv = __int_as_float(e.y);
@@ -514,7 +530,11 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     bm[wq + lane] = 0u;
                 }
                 n_cand += (unsigned long long)__popc(word);
-                if (f_upper) {
+                if (f_upper || blk >= 0) {
+                    // a block item keeps y by Lemma 1 (local pruning): a match scores
+                    // A + dot(x, y') >= t, the blocks that created y hold all of A between
+                    // them, so one of them has A_b >= (t - ||y'||_2) / nblk
+                    const uint32_t mul = blk < 0 ? 1u : (uint32_t)P.nblk;
                     const int sb = (wq + lane) << 5;
                     uint32_t keep = 0u;
                     for (uint32_t wv = word; wv; wv &= wv - 1u) {
@@ -522,7 +542,9 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                         const int sl = sb + b;
                         const uint32_t a = A[sl];
                         const uint32_t code = (pn4s[sl >> 3] >> ((sl & 7) << 2)) & 15u;
-                        if (a + code * PN4_UNIT > thq) keep |= 1u << b; else A[sl] = 0u;
+                        const bool kp = SPLIT ? (uint64_t)a * mul + code * PN4_UNIT > (uint64_t)thq
+                                              : a + code * PN4_UNIT > thq;
+                        if (kp) keep |= 1u << b; else A[sl] = 0u;
                     }
                     word = keep;
                 }
@@ -552,9 +574,11 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                         v = __uint2float_rn(A[s]) * 9.31322574615478515625e-10f;  // 2^-30
                         A[s] = 0u;
                         yc = __ldg(&P.vcand[I.vbase + w0 + s]);
-                        const int ys = yc.y;
+                        const int ys = blk < 0 ? yc.y : 0;  // a block item scores y whole, below
                         bool ok = true;
-                        if (f_upper) {
+                        // (a block item's A is a partial sum: these bounds apply to whole sums
+                        // only, and the block's candidates passed the local test instead)
+                        if (f_upper && blk < 0) {
                             // dot(x, y') <= ||y'||_2 (Cauchy-Schwarz; most candidates stop here),
                             // then the paper's upperbound; both off with NO_UPPERBOUND
                             ok = v + __int_as_float(yc.w) > t - beta;
@@ -564,6 +588,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                             sc = v;
                             stage = ys == 0 ? 1 : (ys <= 16 ? 2 : 3);
                         }
+                        if (blk >= 0) stage = 4;  // kept by the local test: score decided in float64
                     }
                     if (stage == 2) {  // short prefixes: each lane its own candidate
                         n_verified++;
@@ -597,6 +622,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                             stage = 0;
                         }
                     }
+                    if (stage == 4) stage = 1;
                     // inside the band: float64 dot(x, y) over all of y, one candidate at a
                     // time across the warp (x's values from shared memory, exact products)
                     int yfull = 0;
@@ -619,9 +645,23 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                         }
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, emit);
-                    if (emit) elist[ne + __popc(bal & lt_mask)] = make_int2(w0 + s, __float_as_int(sc));
-                    ne += __popc(bal);
+                    if (blk >= 0) {  // block items: pairs to the global list, merged after the join
+                        unsigned long long b = 0;
+                        if (lane == 0 && bal) b = atomicAdd(P.sp_count, (unsigned long long)__popc(bal));
+                        b = __shfl_sync(0xffffffffu, b, 0) + (unsigned long long)__popc(bal & lt_mask);
+                        if (emit && b < (unsigned long long)P.sp_cap) {
+                            P.sp_key[b] = (unsigned long long)lx * (unsigned long long)I.n + (unsigned long long)(w0 + s);
+                            P.sp_score[b] = __float_as_uint(sc);
+                        }
+                    } else {
+                        if (emit) elist[ne + __popc(bal & lt_mask)] = make_int2(w0 + s, __float_as_int(sc));
+                        ne += __popc(bal);
+                    }
                 }
+            }
+            if (blk >= 0) {  // (group-uniform) no run for this (x, window) slot; the barrier
+                gsync(G, g, GT);  // keeps the next window's copies and adds off this window's data
+                continue;
             }
             if (lane == 0) wcnt[gw] = ne;
             gsync(G, g, GT);
@@ -792,9 +832,68 @@ aps_status run_join_graph(aps_index *ix, JoinParams &P, int grid, int smem, unsi
 
 }  // namespace
 
+namespace {
+
+// The work list of a split join: the first `heavy` items of the list (the costliest
+// vectors) become nblk block items each, the rest stay whole.
+__global__ void k_split_items(const int32_t *__restrict__ items, int64_t nitems, int64_t heavy, int nblk,
+                              int32_t *out, int8_t *blk) {
+    const int64_t total = nitems + heavy * (nblk - 1);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        if (k < heavy * nblk) {
+            out[k] = items[k / nblk];
+            blk[k] = (int8_t)(k % nblk);
+        } else {
+            out[k] = items[k - heavy * (nblk - 1)];
+            blk[k] = -1;
+        }
+    }
+}
+
+// First occurrence of each key in a sorted list (the block items of one vector may find a
+// pair twice, with the same score).
+__global__ void k_first_of_key(const unsigned long long *__restrict__ key, int64_t n, int32_t *flag) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        flag[k] = (k == 0 || key[k] != key[k - 1]) ? 1 : 0;
+}
+
+// The split vectors' pairs (key = local x * n + local y, sorted, first occurrences at
+// off[k]) into the staging buffer from `base` on, as the runs of their (x, window) slots.
+__global__ void k_split_place(const unsigned long long *__restrict__ key, const uint32_t *__restrict__ score,
+                              const int32_t *__restrict__ flag, const int64_t *__restrict__ off, int64_t n,
+                              const InstDesc *__restrict__ inst, int64_t base, int2 *stage, Segment *segs,
+                              int32_t *cntq) {
+    const InstDesc I = inst[0];
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[k]) continue;
+        const unsigned long long kk = key[k];
+        const int32_t lx = (int32_t)(kk / (unsigned long long)I.n), y = (int32_t)(kk % (unsigned long long)I.n);
+        const int w = y / I.W;
+        const int64_t qw = I.qwbase + (int64_t)lx * I.nw + w;
+        const int64_t pos = base + off[k];
+        stage[pos] = make_int2(y, (int)score[k]);
+        atomicAdd(&cntq[qw], 1);
+        bool first = k == 0;
+        if (!first) {
+            const unsigned long long pk = key[k - 1];
+            first = (int32_t)(pk / (unsigned long long)I.n) != lx || (int32_t)(pk % (unsigned long long)I.n) / I.W != w;
+        }
+        if (first) {
+            Segment S;
+            S.src = pos;
+            S.cnt = 0;
+            S.i = lx;
+            segs[qw] = S;
+        }
+    }
+}
+
+}  // namespace
+
 void debug_stage_cap(int64_t pairs) { g_stage_cap_once.store(pairs > 0 ? pairs : 0); }
 
-aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::vector<int64_t> *pair_offsets_h) {
+aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::vector<int64_t> *pair_offsets_h,
+                          int nblk, int64_t heavy) {
     cudaStream_t s = ix->stream;
     IndexArrays &d = ix->d;
     const int sms = num_sms();
@@ -811,6 +910,30 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     int need = 0;
     for (int c = 0; c < 4; c++) need = std::max(need, group_bytes(Gs[c]) * Gs[c]);
     APS_CUDA(cudaFuncSetAttribute(join_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
+
+    // the vertical split: the costliest `heavy` vectors as nblk dimension blocks each
+    const bool split = nblk >= 2 && heavy > 0 && ix->k == 1;
+    int split_cls = -1;
+    int64_t nsplit = 0, sp_cap = 0;
+    DBuf<int32_t> items2;
+    DBuf<int8_t> iblk;
+    DBuf<unsigned long long> sp_key;
+    DBuf<uint32_t> sp_score;
+    if (split) {
+        for (int c = 0; c < 4; c++)
+            if (ix->class_begin[c + 1] > ix->class_begin[c]) split_cls = c;
+        const int64_t nitems = ix->class_begin[4] - ix->class_begin[0];
+        nsplit = std::min<int64_t>(heavy, nitems);
+        if (nsplit > 0) {
+            APS_CUDA(cudaFuncSetAttribute(join_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
+            const int64_t total = nitems + nsplit * (nblk - 1);
+            APS_TRY(items2.alloc((size_t)total, s));
+            APS_TRY(iblk.alloc((size_t)total, s));
+            k_split_items<<<grid_for(total, 256), 256, 0, s>>>(ix->items.p, nitems, nsplit, nblk, items2.p, iblk.p);
+            APS_LAUNCH_CHECK();
+            sp_cap = std::max<int64_t>((int64_t)1 << 20, nsplit * 4096);
+        }
+    }
 
     DBuf<int32_t> cntq;
     DBuf<unsigned long long> ctr;  // 0..4 counters, 5 stage count, 6 seg count, 8..11 work
@@ -845,6 +968,10 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     int reruns = 0;
     for (int attempt = 0; attempt < 3; attempt++) {
         APS_TRY(stage.alloc((size_t)stage_cap, s));
+        if (nsplit > 0) {
+            APS_TRY(sp_key.alloc((size_t)sp_cap, s));
+            APS_TRY(sp_score.alloc((size_t)sp_cap, s));
+        }
         if (ix->class_begin[4] <= ix->class_begin[0]) {  // nothing to join: just the resets
             APS_CUDA(cudaMemsetAsync(ctr.p, 0, 16 * sizeof(unsigned long long), s));
             if (ix->nqw) APS_CUDA(cudaMemsetAsync(cntq.p, 0, sizeof(int32_t) * ix->nqw, s));
@@ -877,15 +1004,77 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
             P.scratch = scratch.p;
             P.qmode = 0;
             P.qnw = 1;
+            P.iblk = nullptr;
+            P.nblk = 1;
+            P.sp_key = nullptr;
+            P.sp_score = nullptr;
+            P.sp_count = ctr.p + 12;
+            P.sp_cap = 0;
             APS_CUDA(cudaEventRecord(ev[0], s));
-            APS_TRY(run_join_graph(ix, P, grid, smem, ctr.p, cntq.p, s));
+            if (nsplit > 0) {  // the split work list, one direct launch
+                P.items = items2.p;
+                P.iblk = iblk.p;
+                P.nblk = nblk;
+                P.sp_key = sp_key.p;
+                P.sp_score = sp_score.p;
+                P.sp_cap = sp_cap;
+                for (int c = split_cls + 1; c <= 4; c++) P.cls_begin[c] += nsplit * (nblk - 1);
+                APS_CUDA(cudaMemsetAsync(ctr.p, 0, 16 * sizeof(unsigned long long), s));
+                APS_CUDA(cudaMemsetAsync(cntq.p, 0, sizeof(int32_t) * std::max<int64_t>(ix->nqw, 1), s));
+                join_kernel<false, true><<<grid, JOIN_THREADS, smem, s>>>(P);
+                APS_LAUNCH_CHECK();
+            } else {
+                APS_TRY(run_join_graph(ix, P, grid, smem, ctr.p, cntq.p, s));
+            }
         }
         APS_CUDA(cudaEventRecord(ev[1], s));
         APS_CUDA(cudaMemcpyAsync(ch, ctr.p, sizeof(ch), cudaMemcpyDeviceToHost, s));
         APS_CUDA(cudaStreamSynchronize(s));
         total_pairs = (int64_t)ch[3];
         reserved = (int64_t)ch[5];
-        if (reserved <= stage_cap) break;
+        const int64_t sp_found = nsplit > 0 ? (int64_t)ch[12] : 0;
+        if (reserved <= stage_cap && sp_found <= sp_cap) {
+            if (sp_found > 0) {
+                // the split vectors' pairs: sorted by (x, y), first occurrences kept, placed
+                // after the join's staged runs as the runs of their (x, window) slots
+                const InstDesc &I0 = ix->inst_h[0];
+                APS_TRY(sort_pairs(reinterpret_cast<uint64_t *>(sp_key.p), sp_score.p, sp_found,
+                                   bits_for((uint64_t)I0.n * (uint64_t)I0.n), s));
+                DBuf<int32_t> flag;
+                DBuf<int64_t> off;
+                APS_TRY(flag.alloc((size_t)sp_found, s));
+                APS_TRY(off.alloc((size_t)sp_found + 1, s));
+                k_first_of_key<<<grid_for(sp_found, 256), 256, 0, s>>>(sp_key.p, sp_found, flag.p);
+                APS_LAUNCH_CHECK();
+                APS_TRY(scan_exclusive(flag.p, off.p, sp_found, s));
+                int64_t nuniq = 0;
+                APS_CUDA(cudaMemcpyAsync(&nuniq, off.p + sp_found, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                APS_CUDA(cudaStreamSynchronize(s));
+                if (reserved + nuniq > stage_cap) {  // room after the join's runs
+                    DBuf<int2> grown;
+                    APS_TRY(grown.alloc((size_t)(reserved + nuniq), s));
+                    if (reserved > 0)
+                        APS_CUDA(cudaMemcpyAsync(grown.p, stage.p, sizeof(int2) * reserved, cudaMemcpyDeviceToDevice, s));
+                    std::swap(grown.p, stage.p);
+                    std::swap(grown.n, stage.n);
+                    stage_cap = reserved + nuniq;
+                }
+                k_split_place<<<grid_for(sp_found, 256), 256, 0, s>>>(sp_key.p, sp_score.p, flag.p, off.p, sp_found,
+                                                                     d.inst.p, reserved, stage.p, segs.p, cntq.p);
+                APS_LAUNCH_CHECK();
+                total_pairs += nuniq;
+            }
+            break;
+        }
+        if (sp_found > sp_cap) sp_cap = sp_found + sp_found / 8 + 1024;
+        if (reserved <= stage_cap) {
+            reruns++;
+            if (attempt == 2) {
+                set_error("split pair list overflow persisted");
+                return APS_EOVERFLOW;
+            }
+            continue;
+        }
         // the staging buffer was too small: grow it and run again
         reruns++;
         stage_cap = reserved + (int64_t)sms * 8 * JOIN_STAGE_SLAB;  // plus one slab per group
@@ -939,7 +1128,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     S.visits = (int64_t)ch[0];
     S.candidates = (int64_t)ch[1];
     S.verified = (int64_t)ch[2];
-    S.pairs = (int64_t)ch[3];
+    S.pairs = total_pairs;
     S.band = (int64_t)ch[4];
     S.reruns = reruns;
     S.ms_join = ms_join;

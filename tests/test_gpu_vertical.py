@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from parity import compare
+from parity import compare, row_dot64
 
 pytestmark = pytest.mark.gpu
 
@@ -119,3 +119,62 @@ def test_subunit_norm_join_matches_oracle_on_a_projection(aps):
     with pytest.raises(A.APSError) as e:
         A.aps_build_index(ip, ix, vv, c.n, c.m, tl)
     assert e.value.status == A.EINVAL
+
+
+# ----------------------------------------------- the local pruning inside the join
+
+
+@pytest.mark.parametrize("nblk,heavy,t", [(2, 300, 0.7), (4, 300, 0.6), (3, 10**9, 0.7), (2, 50, 0.9)])
+def test_split_join_matches_oracle_and_plain_join(aps, nblk, heavy, t):
+    """aps_all_pairs_split: the `heavy` costliest vectors joined as nblk dimension blocks with
+    the local threshold of Lemma 1 inside the join, every pair decided exactly; the pair set
+    is the oracle's (and the plain join's) and the output stays in (i, j) order."""
+    import paper_1402_3010_gb300 as A
+
+    rng = np.random.default_rng(90 + nblk)
+    lengths = synth.power_law_lengths(rng, 24000, synth.ALPHA_MEAN50, 1, 600)
+    c = synth.sparse_vectors(24000, 6000, lengths, 1.0, "lognormal", 90 + nblk, rng=rng)
+    tt = f32(t)
+    h = A.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, tt)
+    try:
+        p = A.aps_all_pairs_split(h, nblk, heavy)
+        try:
+            i, j, s = A.pairs_to_numpy(p)
+        finally:
+            A.aps_pairs_free(p)
+        st = A.aps_index_stats(h)
+        q = A.aps_all_pairs(h)
+        try:
+            pi, pj, ps = A.pairs_to_numpy(q)
+        finally:
+            A.aps_pairs_free(q)
+    finally:
+        A.aps_index_free(h)
+    r = compare(i, j, s, oracle.bruteforce(c, tt), tt, c.n, csr=c)
+    assert r["pairs"] > 0 and st["pairs"] == len(i)
+    # the split changes the work, not the pairs: identical to the plain join outside the band
+    keys = i.astype(np.int64) * c.n + j
+    pkeys = pi.astype(np.int64) * c.n + pj
+    diff = np.setxor1d(keys, pkeys)
+    for k in diff.tolist():
+        assert abs(row_dot64(c, *divmod(k, c.n)) - tt) <= 1e-5
+
+
+def test_split_join_rejects_bad_arguments(aps):
+    import paper_1402_3010_gb300 as A
+
+    c, t = synth.config_small(seed=1)
+    h = A.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, t)
+    try:
+        for nblk, heavy in ((1, 10), (9, 10), (2, -1)):
+            with pytest.raises(A.APSError) as e:
+                A.aps_all_pairs_split(h, nblk, heavy)
+            assert e.value.status == A.EINVAL
+        p = A.aps_all_pairs_split(h, 2, 0)  # no heavy vector: the plain join
+        try:
+            i, j, s = A.pairs_to_numpy(p)
+        finally:
+            A.aps_pairs_free(p)
+        compare(i, j, s, oracle.bruteforce(c, f32(t)), f32(t), c.n, csr=c)
+    finally:
+        A.aps_index_free(h)
