@@ -401,7 +401,9 @@ def run_aps(args, rank, world):
         return None
     peak, peak_kind = peaks()
     last = stats[-1]
-    # algorithmic bytes of one join launch: 8 B per posting entry visited, 8 B of (|y'|,
+    # algorithmic bytes of one join launch: 8 B per posting entry visited (Alg. 2's adds: an
+    # entry after x on one of x's lists, with |y| >= minsize; entries the kernel loads and
+    # skips are counted apart, as entries_read), 8 B of (|y'|,
     # maxweight(y')) per candidate, 16 B per dot(x, y') (row pointer + one prefix entry
     # per verified candidate, lower bound) and 8 B per staged output pair
     alg_bytes = 8 * last["visits"] + 8 * last["candidates"] + 16 * last["verified"] + 8 * last["pairs"]
@@ -450,7 +452,7 @@ def run_aps(args, rank, world):
         },
         "phases_ms": {"build": last["ms_build"], "join": last["ms_join"], "output": last["ms_sort"],
                       "join_call": last["ms_total"]},
-        "work": {k: last[k] for k in ("visits", "candidates", "verified", "pairs", "band")},
+        "work": {k: last[k] for k in ("visits", "candidates", "verified", "pairs", "band", "entries_read")},
         "rates_per_s_of_join": {k: last[k] / (jm * 1e-3) for k in ("visits", "candidates", "pairs")},
         "gpu_launches": launches,
         "e2e": e2e,

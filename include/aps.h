@@ -101,7 +101,8 @@ typedef struct aps_graph {
 /* Work counters and phase times of the last aps_all_pairs / aps_query / batch call on
  * an index (all counts are exact; times are CUDA-event milliseconds). */
 typedef struct aps_stats {
-    int64_t visits;       /* posting-list entries read in the accumulation loop */
+    int64_t visits;       /* posting-list entries Alg. 2 adds: on x's lists, y after x (self-join),
+                             |y| >= minsize when minsize is on */
     int64_t candidates;   /* (x, y) pairs with a non-zero partial score */
     int64_t verified;     /* candidates that passed upperbound and got dot(x, y') */
     int64_t pairs;        /* pairs emitted */
@@ -112,6 +113,8 @@ typedef struct aps_stats {
     float ms_join;        /* join kernel launches only (last attempt) */
     float ms_sort;        /* output stage: count scan + gather into (i, j) order */
     float ms_total;       /* whole call */
+    int64_t entries_read; /* posting-list entries loaded by the join (visits plus the entries it
+                             reads and skips: minsize, and ids at or before x in x's first window) */
 } aps_stats;
 
 typedef struct aps_index aps_index;

@@ -94,7 +94,7 @@ class aps_tune_report(ctypes.Structure):
 class aps_stats(ctypes.Structure):
     _fields_ = [("visits", _i64), ("candidates", _i64), ("verified", _i64), ("pairs", _i64),
                 ("band", _i64), ("evaluations", _i64), ("reruns", _i64), ("ms_build", _f32),
-                ("ms_join", _f32), ("ms_sort", _f32), ("ms_total", _f32)]
+                ("ms_join", _f32), ("ms_sort", _f32), ("ms_total", _f32), ("entries_read", _i64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

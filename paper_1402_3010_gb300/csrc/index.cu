@@ -342,8 +342,10 @@ __global__ void k_wptr(const InstDesc *__restrict__ inst, int k, int64_t M, cons
 }
 
 // Join work list: every vector with later candidates in its instance, keyed by
-// (size class, decreasing estimated cost) so that the persistent join takes the most
-// expensive queries first (least-loaded-first idea of the vertical algorithm's binning).
+// (class, decreasing estimated cost) so that the persistent join takes the most expensive
+// queries first (least-loaded-first idea of the vertical algorithm's binning). Classes 0-3
+// are the instance's tile shape (G = 1, 2, 4, 8 query groups per CTA); class 4 holds the
+// vectors with a single component, which the join streams one warp per vector.
 __global__ void k_item_keys(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
                             const int64_t *__restrict__ lptr, const int32_t *__restrict__ vinst,
                             const InstDesc *__restrict__ inst, int64_t N, uint64_t *keys, uint32_t *vals,
@@ -368,11 +370,11 @@ __global__ void k_item_keys(const int64_t *__restrict__ cptr, const int32_t *__r
             const double lists = (double)lsum;
             double cost = lists * later / (double)I.n + later / 8.0 + 32.0;
             uint64_t c = cost >= 4294967295.0 ? 0xffffffffull : (uint64_t)cost;
-            int cls = I.G == 1 ? 0 : I.G == 2 ? 1 : I.G == 4 ? 2 : 3;
+            const int cls = b - a == 1 ? 4 : I.G == 1 ? 0 : I.G == 2 ? 1 : I.G == 4 ? 2 : 3;
             key = ((uint64_t)cls << 32) | (0xffffffffull - c);
             atomicAdd(&class_count[cls], 1ull);
         } else {
-            key = 4ull << 32;
+            key = 5ull << 32;
         }
         keys[x] = key;
         vals[x] = (uint32_t)x;
@@ -481,7 +483,7 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     DBuf<unsigned long long> err;
     APS_TRY(erow.alloc((size_t)nnz, s));
     APS_TRY(vout.alloc((size_t)nnz, s));
-    APS_TRY(err.alloc(4, s));
+    APS_TRY(err.alloc(JOIN_NCLS, s));
     APS_CUDA(cudaMemsetAsync(err.p, 0xff, sizeof(unsigned long long), s));
     APS_CUDA(cudaMemsetAsync(err.p + 1, 0, 3 * sizeof(unsigned long long), s));
 
@@ -593,23 +595,23 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
         DBuf<uint32_t> vals;
         APS_TRY(keys.alloc((size_t)std::max<int64_t>(N, 1), s));
         APS_TRY(vals.alloc((size_t)std::max<int64_t>(N, 1), s));
-        unsigned long long *cc = err.p;  // reuse 4 counters
-        APS_CUDA(cudaMemsetAsync(cc, 0, 4 * sizeof(unsigned long long), s));
+        unsigned long long *cc = err.p;  // reused: one counter per class
+        APS_CUDA(cudaMemsetAsync(cc, 0, JOIN_NCLS * sizeof(unsigned long long), s));
         if (N > 0) {
             k_item_keys<<<gN, T256, 0, s>>>(d.cptr.p, d.crank.p, d.lptr.p, d.vinst.p, d.inst.p, N, keys.p, vals.p,
                                             cc);
             APS_LAUNCH_CHECK();
             APS_TRY(sort_pairs(keys.p, vals.p, N, 35, s));
         }
-        unsigned long long cnt_h[4] = {0, 0, 0, 0};
+        unsigned long long cnt_h[JOIN_NCLS] = {};
         APS_CUDA(cudaMemcpyAsync(cnt_h, cc, sizeof(cnt_h), cudaMemcpyDeviceToHost, s));
         APS_CUDA(cudaStreamSynchronize(s));
         int64_t acc = 0;
-        for (int c = 0; c < 4; c++) {
+        for (int c = 0; c < JOIN_NCLS; c++) {
             ix->class_begin[c] = acc;
             acc += (int64_t)cnt_h[c];
         }
-        ix->class_begin[4] = acc;
+        ix->class_begin[JOIN_NCLS] = acc;
         APS_TRY(ix->items.alloc((size_t)std::max<int64_t>(acc, 1), s));
         if (acc > 0) {
             k_take_vals<<<grid_for(acc, T256), T256, 0, s>>>(vals.p, acc, ix->items.p);

@@ -44,11 +44,12 @@ struct JoinParams {
     const InstDesc *inst;
     const int32_t *vinst;
     const int32_t *items;
-    // size classes, taken in order by one persistent launch: class c is the work-list range
-    // [cls_begin[c], cls_begin[c + 1]) run with cls_G[c] query groups per CTA
+    // classes, taken in order by one persistent launch: class c is the work-list range
+    // [cls_begin[c], cls_begin[c + 1]) run with cls_G[c] query groups per CTA, or, when
+    // cls_G[c] is 0, one warp per single-component vector
     int ncls;
-    int cls_G[4];
-    int64_t cls_begin[5];
+    int cls_G[JOIN_NCLS];
+    int64_t cls_begin[JOIN_NCLS + 1];
     const int2 *crow;    // rank-ordered rows {rank, value}
     const int4 *vmeta;   // {row offset, |x|, |x'|, maxweight(x')}
     const int4 *vcand;   // {row offset, |y'|, maxweight(y'), ||y'||_2 bound}
@@ -73,7 +74,7 @@ struct JoinParams {
     int64_t stage_slab;
     Segment *segs;                    // [slots]: the run of slot qw
     int32_t *cntq;
-    unsigned long long *counters;  // visits, candidates, verified, pairs, band
+    unsigned long long *counters;  // visits, candidates, verified, pairs, band; [6] entries read
     unsigned long long *work;       // [ncls] work-list cursors
     int2 *scratch;                  // per-warp lists of emitted pairs, JOIN_ECAP each
     // query mode: items are external query rows matched against every indexed vector
@@ -181,7 +182,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <bool CREATE, bool FIRST>
 __device__ __forceinline__ void walk_chunk(const int2 *__restrict__ seg, const int cnt, const int off, const float cxv,
                                            uint32_t *A, uint32_t *bm, const uint32_t smin_tag, const int32_t idmask,
-                                           const int w0, const int lo, const int lane) {
+                                           const int w0, const int lo, const int lane, uint32_t &nv) {
     const int rem = cnt - off - lane;  // entries from this lane's first one to the segment's end
     const int2 *pp = seg + off + lane;
     int2 ent[4];
@@ -192,6 +193,7 @@ __device__ __forceinline__ void walk_chunk(const int2 *__restrict__ seg, const i
         if (u * 32 >= rem || (uint32_t)ent[u].x < smin_tag) continue;  // past the end; minsize
         const int slot = (ent[u].x & idmask) - w0;
         if (FIRST && slot < lo) continue;
+        nv++;  // an entry Alg. 2 visits: y after x, |y| >= minsize
         const uint32_t q = __float2uint_ru(cxv * __int_as_float(ent[u].y));
         const uint32_t old = A[slot];
         if (CREATE) {
@@ -218,7 +220,8 @@ __device__ __forceinline__ void walk_chunks(int ch, const int che, int cc, const
                                             const int32_t *c_cnt, const int32_t *c_ch0, const float *c_xv,
                                             const int2 *__restrict__ post, uint32_t *A, uint32_t *bm,
                                             const uint32_t smin_tag, const int32_t idmask, const int w0, const int lo,
-                                            const int lane) {
+                                            const int lane, unsigned long long &n_visits) {
+    uint32_t nv = 0;
     const int2 *seg = post + c_start[cc];
     int cnt = c_cnt[cc], cch0 = c_ch0[cc], cnext = c_ch0[cc + 1];
     float cxv = c_xv[cc] * 1073741824.f;  // x's value scaled by 2^30 (exact)
@@ -231,8 +234,9 @@ __device__ __forceinline__ void walk_chunks(int ch, const int che, int cc, const
             cnext = c_ch0[cc + 1];
             cxv = c_xv[cc] * 1073741824.f;
         }
-        walk_chunk<CREATE, FIRST>(seg, cnt, (ch - cch0) << 7, cxv, A, bm, smin_tag, idmask, w0, lo, lane);
+        walk_chunk<CREATE, FIRST>(seg, cnt, (ch - cch0) << 7, cxv, A, bm, smin_tag, idmask, w0, lo, lane, nv);
     }
+    n_visits += nv;
 }
 
 // The same with the (at most 32) components of a short x held in registers, lane c holding
@@ -241,7 +245,8 @@ template <bool CREATE, bool FIRST>
 __device__ __forceinline__ void walk_chunks_r(int ch, const int che, int cc, const int64_t st, const int cnt_l,
                                               const int ch0_l, const float xv_l, const int2 *__restrict__ post,
                                               uint32_t *A, uint32_t *bm, const uint32_t smin_tag, const int32_t idmask,
-                                              const int w0, const int lo, const int lane) {
+                                              const int w0, const int lo, const int lane, unsigned long long &n_visits) {
+    uint32_t nv = 0;
     const int2 *seg = post + __shfl_sync(0xffffffffu, st, cc);
     int cnt = __shfl_sync(0xffffffffu, cnt_l, cc), cch0 = __shfl_sync(0xffffffffu, ch0_l, cc);
     float cxv = __shfl_sync(0xffffffffu, xv_l, cc) * 1073741824.f;
@@ -253,8 +258,9 @@ __device__ __forceinline__ void walk_chunks_r(int ch, const int che, int cc, con
             cch0 = __shfl_sync(0xffffffffu, ch0_l, cc);
             cxv = __shfl_sync(0xffffffffu, xv_l, cc) * 1073741824.f;
         }
-        walk_chunk<CREATE, FIRST>(seg, cnt, (ch - cch0) << 7, cxv, A, bm, smin_tag, idmask, w0, lo, lane);
+        walk_chunk<CREATE, FIRST>(seg, cnt, (ch - cch0) << 7, cxv, A, bm, smin_tag, idmask, w0, lo, lane, nv);
     }
+    n_visits += nv;
 }
 
 // dot(x, y') over the |y'| leading (unindexed) entries of y's rank-ordered row, by one
@@ -275,6 +281,145 @@ __device__ __forceinline__ float dot_prefix(const int2 *__restrict__ yr, int ys,
     return acc;
 }
 
+// First position in [a, b) of a posting list (ids increasing) whose id exceeds lx, or b
+// when none does: a 32-way search by the whole warp (each step probes 32 evenly spaced
+// entries and keeps the one gap that holds the answer).
+__device__ __forceinline__ int64_t first_after(const int2 *__restrict__ post, int64_t a, int64_t b, const int32_t lx,
+                                               const int32_t idmask, const int lane) {
+    while (b - a > 32) {
+        const int64_t step = (b - a + 31) >> 5;
+        const int64_t pos = a + (int64_t)lane * step;
+        const bool past = pos >= b || (__ldg(&post[pos].x) & idmask) > lx;
+        const unsigned m = __ballot_sync(0xffffffffu, past);
+        if (m & 1u) return a;  // the range's first entry is already after x
+        if (m == 0u) {
+            a += 31 * step + 1;  // every probe at or before x: the answer lies after the last one
+        } else {
+            const int f = __ffs(m) - 1;  // probe f is past x, probe f - 1 is not
+            b = min(b, a + (int64_t)f * step);
+            a += (int64_t)(f - 1) * step + 1;
+        }
+    }
+    const int64_t pos = a + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, pos < b && (__ldg(&post[pos].x) & idmask) > lx);
+    return m ? a + (__ffs(m) - 1) : b;
+}
+
+// The vectors with a single component r (value xv) (Alg. 2 for |x| = 1). Every entry
+// (y, w) of r's posting list with y after x and |y| >= minsize is a candidate, and its
+// accumulated score xv * w is already its whole score: x has no other component, and
+// dot(x, y') = 0 since r lies in y's indexed part. So no accumulator and no windows: one
+// warp per vector finds the later part of the list, streams it once to count the matches
+// (decided like the windowed path: float32 outside a band of beta around t, float64
+// inside it) and once more to write them, in increasing y, as x's run in its first
+// window's slot, from a staging slab the warp reserves in bulk.
+__device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long long *work, const int64_t item_begin,
+                                            const int64_t item_end, const bool f_minsize, const bool f_remscore,
+                                            unsigned long long &n_visits, unsigned long long &n_cand,
+                                            unsigned long long &n_pairs, unsigned long long &n_band,
+                                            unsigned long long &n_read) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t wslab = max((int64_t)32, P.stage_slab / 8);
+    int64_t sb = 0, su = 0, ss = 0;  // this warp's staging slab: base, used, size
+    for (;;) {
+        unsigned long long iw = 0;
+        if (lane == 0) iw = atomicAdd(work, 1ull);
+        const int64_t it = (int64_t)__shfl_sync(0xffffffffu, iw, 0) + item_begin;
+        if (it >= item_end) break;
+        const int64_t x = P.items[it];
+        const InstDesc I = P.inst[P.vinst[x]];
+        const int32_t lx = (int32_t)(x - I.vbase);
+        const int4 xm = P.vmeta[x];
+        if (f_remscore && P.qsplit[x] >= xm.y) continue;  // remscore < t: no candidate at all
+        const int2 xe = P.crow[xm.x];
+        const float xv = __int_as_float(xe.y);
+        const float t = I.t;
+        const float beta = fmaxf(1e-5f, 3.f * 1.1920929e-7f);  // (|x| + 2) * 2^-23 with |x| = 1
+        const float mwx = P.mw[x];
+        int smin = 0;  // minsize, bounded as in the windowed path
+        if (f_minsize && I.packed && mwx > 0.f)
+            smin = (int)ceilf(fminf(__fdiv_rd(__fsub_rd(t, beta), __fmul_ru(mwx, 1.0020001f)), 255.f));
+        const uint32_t smin_tag = (uint32_t)max(smin, 0) << 24;
+        const int32_t idmask = I.packed ? 0x00ffffff : 0x7fffffff;
+        const int64_t R = (int64_t)I.rbase + xe.x;
+        const int64_t ls = P.lptr[R], le = P.lptr[R + 1];
+        const int wf = (lx + 1) / I.W;  // the window of x's successor
+        int64_t a = ls, b = le;
+        if (I.nw > 1) {  // the answer lies in that window's part of the list, or right after it
+            const int32_t *wp = P.wptr + I.wbase + (int64_t)xe.x * (I.nw + 1);
+            a = ls + wp[wf];
+            b = ls + wp[wf + 1];
+        }
+        const int64_t first = first_after(P.post, a, b, lx, idmask, lane);
+        if (lane == 0) n_read += (unsigned long long)(le - first);
+        // pass 1: count the matches; pass 2: write them
+        int cnt = 0;
+        int64_t dst = 0;
+        bool wr = false;
+        for (int pass = 0; pass < 2; pass++) {
+            int k = 0;  // matches written so far
+            for (int64_t p0 = first; p0 < le; p0 += 128) {
+                int2 e[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int64_t p = p0 + u * 32 + lane;
+                    e[u] = p < le ? __ldg(&P.post[p]) : make_int2(0, 0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int64_t p = p0 + u * 32 + lane;
+                    bool m = false;
+                    float sc = 0.f;
+                    if (p < le && (uint32_t)e[u].x >= smin_tag) {
+                        if (pass == 0) { n_visits++; n_cand++; }
+                        sc = xv * __int_as_float(e[u].y);
+                        if (sc >= t + beta) {
+                            m = true;
+                        } else if (sc > t - beta) {  // inside the band: the exact product decides
+                            const double ex = (double)xv * (double)__int_as_float(e[u].y);
+                            if (pass == 0) n_band++;
+                            m = ex >= (double)t;
+                            sc = (float)ex;
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, m);
+                    if (pass == 1 && m) P.stage[dst + k + __popc(bal & lt_mask)] = make_int2(e[u].x & idmask, __float_as_int(sc));
+                    k += __popc(bal);
+                }
+            }
+            if (pass == 0) {
+                cnt = k;
+                if (cnt == 0) break;
+                if (su + cnt > ss) {  // a new slab: one global atomic per slab
+                    const int64_t want = max(wslab, (int64_t)cnt);
+                    unsigned long long bw = 0;
+                    if (lane == 0) bw = atomicAdd(P.stage_count, (unsigned long long)want);
+                    sb = (int64_t)__shfl_sync(0xffffffffu, bw, 0);
+                    su = 0;
+                    ss = want;
+                }
+                dst = sb + su;
+                su += cnt;
+                wr = dst + cnt <= P.stage_cap;
+                if (lane == 0) {
+                    const int64_t qw = I.qwbase + (int64_t)lx * I.nw + wf;
+                    P.cntq[qw] = cnt;
+                    if (wr) {
+                        Segment S;
+                        S.src = dst;
+                        S.cnt = cnt;
+                        S.i = lx;
+                        P.segs[qw] = S;
+                    }
+                    n_pairs += (unsigned long long)cnt;
+                }
+                if (!wr) break;  // no room: the host grows the staging buffer and runs again
+            }
+        }
+    }
+}
+
 // QMODE: external queries against the index (P.qmode = 1); SPLIT: a self-join whose work
 // list may hold dimension-block items (P.iblk). Each is compiled separately, so that the
 // plain self-join carries none of the other paths' state.
@@ -284,7 +429,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     const bool f_minsize = !(P.flags & APS_NO_MINSIZE);
     const bool f_remscore = !(P.flags & APS_NO_REMSCORE);
     const bool f_upper = !(P.flags & APS_NO_UPPERBOUND);
-    unsigned long long n_visits = 0, n_cand = 0, n_verified = 0, n_band = 0, n_pairs = 0;
+    unsigned long long n_visits = 0, n_cand = 0, n_verified = 0, n_band = 0, n_pairs = 0, n_read = 0;
     // A CTA that finds a class's work list empty moves on to the next class and re-carves
     // its shared memory for that class's G, so the classes share one launch and one tail.
     for (int cls = 0; cls < P.ncls; cls++) {
@@ -292,6 +437,10 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     if (item_end <= item_begin) continue;
     const int G = P.cls_G[cls];
     unsigned long long *const work = P.work + cls;
+    if (!QMODE && G == 0) {  // single-component vectors: one warp each, no shared memory
+        stream_singles(P, work, item_begin, item_end, f_minsize, f_remscore, n_visits, n_cand, n_pairs, n_band, n_read);
+        continue;
+    }
     const int GT = JOIN_THREADS / G;
     const int g = threadIdx.x / GT, gt = threadIdx.x % GT;
     const int lane = gt & 31, gw = gt >> 5, NW = GT >> 5;
@@ -401,7 +550,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     }
                     cnt = (int32_t)(le - ls);
                     st = ls;
-                    if (gw == 0) n_visits += (unsigned long long)cnt;
+                    if (gw == 0) n_read += (unsigned long long)cnt;
                 }
                 const int nch = (cnt + 127) >> 7;
                 int nchk;
@@ -419,11 +568,11 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     // the last component with entries whose first chunk is at or before ch
                     const int cc = 31 - __clz(__ballot_sync(0xffffffffu, nch > 0 && ch0 <= ch));
                     if (phase == 0) {
-                        if (lo > 0) walk_chunks_r<true, true>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
-                        else walk_chunks_r<true, false>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
+                        if (lo > 0) walk_chunks_r<true, true>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
+                        else walk_chunks_r<true, false>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
                     } else {
-                        if (lo > 0) walk_chunks_r<false, true>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
-                        else walk_chunks_r<false, false>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
+                        if (lo > 0) walk_chunks_r<false, true>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
+                        else walk_chunks_r<false, false>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
                     }
                 }
                 cp_async_wait_all();  // the window's codes have landed (visible after the barrier)
@@ -448,7 +597,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     }
                     cnt = (int32_t)(le - ls);
                     st = ls;
-                    n_visits += (unsigned long long)cnt;  // every entry of the window's list is walked
+                    n_read += (unsigned long long)cnt;  // every entry of the window's list is loaded
                 }
                 // scan of (chunks, non-empty, non-empty creating) packed in one int64
                 const int64_t nch = (cnt + 127) >> 7;
@@ -496,11 +645,11 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     // four specialisations: creating or updating, first window (ids at or
                     // below x present) or not
                     if (phase == 0) {
-                        if (lo > 0) walk_chunks<true, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
-                        else walk_chunks<true, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
+                        if (lo > 0) walk_chunks<true, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
+                        else walk_chunks<true, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
                     } else {
-                        if (lo > 0) walk_chunks<false, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
-                        else walk_chunks<false, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane);
+                        if (lo > 0) walk_chunks<false, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
+                        else walk_chunks<false, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
                     }
                 }
                 cp_async_wait_all();  // the window's codes have landed (visible after the barrier)
@@ -709,12 +858,12 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     __syncthreads();  // every group is done with this class's layout of shared memory
     }
     // flush counters (warp-reduce, one atomic per warp)
-    unsigned long long v5[5] = {n_visits, n_cand, n_verified, n_pairs, n_band};
+    unsigned long long v6[6] = {n_visits, n_cand, n_verified, n_pairs, n_band, n_read};
 #pragma unroll
-    for (int k = 0; k < 5; k++) {
-        unsigned long long v = v5[k];
+    for (int k = 0; k < 6; k++) {
+        unsigned long long v = v6[k];
         for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&P.counters[k], v);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&P.counters[k < 5 ? k : 6], v);
     }
 }
 
@@ -744,23 +893,25 @@ __global__ void k_inst_offsets(const InstDesc *__restrict__ inst, int k, const i
         out[i] = i < k ? qwoff[inst[i].qwbase] : qwoff[nqw];
 }
 
-// The index's size classes as one launch's class list. Returns the CTA count (enough for
-// every class's groups, at most max_ctas) and sets *smem to the largest class layout used.
+// The index's work-list classes as one launch's class list. Returns the CTA count (enough
+// for every class's groups, or warps for the single-component class, at most max_ctas) and
+// sets *smem to the largest class layout used.
 int set_classes(JoinParams &P, const aps_index *ix, int max_ctas, int *smem) {
-    static const int Gs[4] = {1, 2, 4, 8};
-    P.ncls = 4;
-    int64_t groups = 0;
+    static const int Gs[JOIN_NCLS] = {1, 2, 4, 8, 0};
+    P.ncls = JOIN_NCLS;
+    int64_t ctas = 0;
     *smem = 0;
-    for (int c = 0; c < 4; c++) {
+    for (int c = 0; c < JOIN_NCLS; c++) {
         P.cls_G[c] = Gs[c];
         P.cls_begin[c] = ix->class_begin[c];
         const int64_t ni = ix->class_begin[c + 1] - ix->class_begin[c];
         if (ni <= 0) continue;
-        groups += (ni + Gs[c] - 1) / Gs[c];
-        *smem = std::max(*smem, group_bytes(Gs[c]) * Gs[c]);
+        const int per_cta = Gs[c] > 0 ? Gs[c] : NWARPS;
+        ctas = std::max(ctas, (ni + per_cta - 1) / per_cta);
+        if (Gs[c] > 0) *smem = std::max(*smem, group_bytes(Gs[c]) * Gs[c]);
     }
-    P.cls_begin[4] = ix->class_begin[4];
-    return (int)std::min<int64_t>(max_ctas, std::max<int64_t>(groups, 1));
+    P.cls_begin[JOIN_NCLS] = ix->class_begin[JOIN_NCLS];
+    return (int)std::min<int64_t>(max_ctas, std::max<int64_t>(ctas, 1));
 }
 
 // The join phase (reset the counters and the per-slot pair counts, then the persistent
@@ -890,6 +1041,10 @@ __global__ void k_split_place(const unsigned long long *__restrict__ key, const 
 
 }  // namespace
 
+// Staging slots one CTA can reserve and leave unused: a slab per group of every windowed
+// class (1 + 2 + 4 + 8 groups) and a slab per warp of the single-component class.
+int64_t join_slab_slack() { return 15 * (int64_t)JOIN_STAGE_SLAB + (int64_t)NWARPS * (JOIN_STAGE_SLAB / 8); }
+
 void debug_stage_cap(int64_t pairs) { g_stage_cap_once.store(pairs > 0 ? pairs : 0); }
 
 aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::vector<int64_t> *pair_offsets_h,
@@ -920,10 +1075,12 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     DBuf<unsigned long long> sp_key;
     DBuf<uint32_t> sp_score;
     if (split) {
+        // block items come from the windowed classes (G = 1 ... 8), never from the
+        // single-component class that follows them
         for (int c = 0; c < 4; c++)
             if (ix->class_begin[c + 1] > ix->class_begin[c]) split_cls = c;
-        const int64_t nitems = ix->class_begin[4] - ix->class_begin[0];
-        nsplit = std::min<int64_t>(heavy, nitems);
+        const int64_t nitems = ix->class_begin[JOIN_NCLS] - ix->class_begin[0];
+        nsplit = std::min<int64_t>(heavy, ix->class_begin[4] - ix->class_begin[0]);
         if (nsplit > 0) {
             APS_CUDA(cudaFuncSetAttribute(join_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
             const int64_t total = nitems + nsplit * (nblk - 1);
@@ -936,7 +1093,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     }
 
     DBuf<int32_t> cntq;
-    DBuf<unsigned long long> ctr;  // 0..4 counters, 5 stage count, 6 seg count, 8..11 work
+    DBuf<unsigned long long> ctr;  // 0..4 counters, 5 stage count, 6 entries read, 8..12 work, 13 split pairs
     APS_TRY(cntq.alloc((size_t)std::max<int64_t>(ix->nqw, 1), s));
     APS_TRY(ctr.alloc(16, s));
     // Staging capacity: the index's own hint, else the last join of this process; a join
@@ -947,7 +1104,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
         // no join of this process has sized the staging yet: take room for every possible
         // pair plus one slab per group, but at most an eighth of the free device memory
         // and 2^28 pairs, so that a first join rarely has to run twice
-        int64_t most = (int64_t)sms * 8 * JOIN_STAGE_SLAB;
+        int64_t most = (int64_t)sms * join_slab_slack();
         for (const InstDesc &I : ix->inst_h) most += (int64_t)I.n * (I.n - 1) / 2;
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
@@ -972,7 +1129,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
             APS_TRY(sp_key.alloc((size_t)sp_cap, s));
             APS_TRY(sp_score.alloc((size_t)sp_cap, s));
         }
-        if (ix->class_begin[4] <= ix->class_begin[0]) {  // nothing to join: just the resets
+        if (ix->class_begin[JOIN_NCLS] <= ix->class_begin[0]) {  // nothing to join: just the resets
             APS_CUDA(cudaMemsetAsync(ctr.p, 0, 16 * sizeof(unsigned long long), s));
             if (ix->nqw) APS_CUDA(cudaMemsetAsync(cntq.p, 0, sizeof(int32_t) * ix->nqw, s));
             APS_CUDA(cudaEventRecord(ev[0], s));
@@ -1008,7 +1165,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
             P.nblk = 1;
             P.sp_key = nullptr;
             P.sp_score = nullptr;
-            P.sp_count = ctr.p + 12;
+            P.sp_count = ctr.p + 13;
             P.sp_cap = 0;
             APS_CUDA(cudaEventRecord(ev[0], s));
             if (nsplit > 0) {  // the split work list, one direct launch
@@ -1018,7 +1175,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
                 P.sp_key = sp_key.p;
                 P.sp_score = sp_score.p;
                 P.sp_cap = sp_cap;
-                for (int c = split_cls + 1; c <= 4; c++) P.cls_begin[c] += nsplit * (nblk - 1);
+                for (int c = split_cls + 1; c <= JOIN_NCLS; c++) P.cls_begin[c] += nsplit * (nblk - 1);
                 APS_CUDA(cudaMemsetAsync(ctr.p, 0, 16 * sizeof(unsigned long long), s));
                 APS_CUDA(cudaMemsetAsync(cntq.p, 0, sizeof(int32_t) * std::max<int64_t>(ix->nqw, 1), s));
                 join_kernel<false, true><<<grid, JOIN_THREADS, smem, s>>>(P);
@@ -1032,7 +1189,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
         APS_CUDA(cudaStreamSynchronize(s));
         total_pairs = (int64_t)ch[3];
         reserved = (int64_t)ch[5];
-        const int64_t sp_found = nsplit > 0 ? (int64_t)ch[12] : 0;
+        const int64_t sp_found = nsplit > 0 ? (int64_t)ch[13] : 0;
         if (reserved <= stage_cap && sp_found <= sp_cap) {
             if (sp_found > 0) {
                 // the split vectors' pairs: sorted by (x, y), first occurrences kept, placed
@@ -1077,7 +1234,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
         }
         // the staging buffer was too small: grow it and run again
         reruns++;
-        stage_cap = reserved + (int64_t)sms * 8 * JOIN_STAGE_SLAB;  // plus one slab per group
+        stage_cap = reserved + (int64_t)sms * join_slab_slack();  // plus every slab a CTA can leave unfilled
         if (attempt == 2) {
             set_error("pair staging overflow persisted");
             return APS_EOVERFLOW;
@@ -1130,6 +1287,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     S.verified = (int64_t)ch[2];
     S.pairs = total_pairs;
     S.band = (int64_t)ch[4];
+    S.entries_read = (int64_t)ch[6];
     S.reruns = reruns;
     S.ms_join = ms_join;
     S.ms_sort = ms_sort;
@@ -1274,7 +1432,7 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
     APS_CUDA(cudaFuncSetAttribute(join_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
     APS_CUDA(cudaMemsetAsync(ctr, 0, 16 * sizeof(unsigned long long), s));
     APS_CUDA(cudaMemsetAsync(cntq, 0, sizeof(int32_t) * nqw, s));
-    if (ix->class_begin[4] > ix->class_begin[0]) {
+    if (ix->class_begin[JOIN_NCLS] > ix->class_begin[0]) {
         JoinParams P;
         P.inst = d.inst.p;
         P.vinst = d.vinst.p;
@@ -1336,6 +1494,7 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
     S.verified = (int64_t)ch[2];
     S.pairs = (int64_t)ch[3];
     S.band = (int64_t)ch[4];
+    S.entries_read = (int64_t)ch[6];
     S.reruns = 0;
     S.ms_join = S.ms_sort = S.ms_total = 0.f;
     S.evaluations = 0;
@@ -1472,6 +1631,7 @@ aps_status join_queries(const aps_index *ix, const QueryArrays &qa, float t, uin
         stats->verified = (int64_t)ch[2];
         stats->pairs = (int64_t)ch[3];
         stats->band = (int64_t)ch[4];
+        stats->entries_read = (int64_t)ch[6];
         stats->evaluations = nq * (int64_t)I.n;
         stats->ms_join = mj;
         stats->ms_sort = mo;
