@@ -35,7 +35,9 @@ namespace aps {
 constexpr int JOIN_THREADS = 1024;
 constexpr int JOIN_WMAX = 40960;  // accumulator slots of a whole CTA (160 KB)
 constexpr int JOIN_RMAX = 1536;   // dense rank table for dot(x, y') lookups (6 KB)
-constexpr int JOIN_XCAP = 1536;   // x's row kept in shared memory when |x| <= XCAP / G
+constexpr int JOIN_XCAP = 1280;   // x's row kept in shared memory when |x| <= XCAP / G
+// (so that every class layout of a CTA plus the join kernel's 1.5 KB of per-warp counters
+// fits the 227 KB of shared memory a CTA can have)
 // per-warp list of emitted pairs of one window: a warp scans at most W/NW slots rounded
 // up to 128 (W/NW = 1280 for every group shape)
 constexpr int JOIN_ECAP = JOIN_WMAX / (JOIN_THREADS / 32) + 128;

@@ -104,6 +104,14 @@ __host__ __device__ constexpr int group_bytes(int G) {
            + 8 * 8;                                  // broadcast and the staging slab
 }
 
+// every class layout of a CTA plus the kernel's per-warp counters (static shared memory)
+// within the 227 KB a CTA can opt into on this part
+constexpr int JOIN_SMEM_LIMIT = 232448;
+static_assert(group_bytes(1) * 1 + NWARPS * 6 * 8 <= JOIN_SMEM_LIMIT, "G = 1 layout too large");
+static_assert(group_bytes(2) * 2 + NWARPS * 6 * 8 <= JOIN_SMEM_LIMIT, "G = 2 layout too large");
+static_assert(group_bytes(4) * 4 + NWARPS * 6 * 8 <= JOIN_SMEM_LIMIT, "G = 4 layout too large");
+static_assert(group_bytes(8) * 8 + NWARPS * 6 * 8 <= JOIN_SMEM_LIMIT, "G = 8 layout too large");
+
 __device__ __forceinline__ void gsync(int G, int g, int GT) {
     if (G == 1)
         __syncthreads();
@@ -177,6 +185,22 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// A thread's work counters, 32-bit: folded (warp-reduced) into its warp's 64-bit totals in
+// shared memory after every item, so no 64-bit register pair stays live across the loops.
+struct Ctr {
+    uint32_t visits = 0, cand = 0, verified = 0, pairs = 0, band = 0, read = 0;
+};
+__device__ __forceinline__ void ctr_flush(Ctr &c, unsigned long long *wtot, const int lane) {
+    uint32_t v[6] = {c.visits, c.cand, c.verified, c.pairs, c.band, c.read};
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        if (lane == 0) wtot[k] += v[k];
+    }
+    c = Ctr();
+}
+
 // One 128-entry chunk of a segment: entries off .. off + 127 of seg[0, cnt), lane l taking
 // off + l, off + l + 32, ... (see walk_chunks).
 template <bool CREATE, bool FIRST>
@@ -220,7 +244,7 @@ __device__ __forceinline__ void walk_chunks(int ch, const int che, int cc, const
                                             const int32_t *c_cnt, const int32_t *c_ch0, const float *c_xv,
                                             const int2 *__restrict__ post, uint32_t *A, uint32_t *bm,
                                             const uint32_t smin_tag, const int32_t idmask, const int w0, const int lo,
-                                            const int lane, unsigned long long &n_visits) {
+                                            const int lane, uint32_t &n_visits) {
     uint32_t nv = 0;
     const int2 *seg = post + c_start[cc];
     int cnt = c_cnt[cc], cch0 = c_ch0[cc], cnext = c_ch0[cc + 1];
@@ -245,7 +269,7 @@ template <bool CREATE, bool FIRST>
 __device__ __forceinline__ void walk_chunks_r(int ch, const int che, int cc, const int64_t st, const int cnt_l,
                                               const int ch0_l, const float xv_l, const int2 *__restrict__ post,
                                               uint32_t *A, uint32_t *bm, const uint32_t smin_tag, const int32_t idmask,
-                                              const int w0, const int lo, const int lane, unsigned long long &n_visits) {
+                                              const int w0, const int lo, const int lane, uint32_t &n_visits) {
     uint32_t nv = 0;
     const int2 *seg = post + __shfl_sync(0xffffffffu, st, cc);
     int cnt = __shfl_sync(0xffffffffu, cnt_l, cc), cch0 = __shfl_sync(0xffffffffu, ch0_l, cc);
@@ -315,14 +339,14 @@ __device__ __forceinline__ int64_t first_after(const int2 *__restrict__ post, in
 // window's slot, from a staging slab the warp reserves in bulk.
 __device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long long *work, const int64_t item_begin,
                                             const int64_t item_end, const bool f_minsize, const bool f_remscore,
-                                            unsigned long long &n_visits, unsigned long long &n_cand,
-                                            unsigned long long &n_pairs, unsigned long long &n_band,
-                                            unsigned long long &n_read) {
+                                            unsigned long long *wtot) {
     const int lane = threadIdx.x & 31;
+    Ctr ct;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t wslab = max((int64_t)32, P.stage_slab / 8);
     int64_t sb = 0, su = 0, ss = 0;  // this warp's staging slab: base, used, size
     for (;;) {
+        ctr_flush(ct, wtot, lane);
         unsigned long long iw = 0;
         if (lane == 0) iw = atomicAdd(work, 1ull);
         const int64_t it = (int64_t)__shfl_sync(0xffffffffu, iw, 0) + item_begin;
@@ -352,7 +376,7 @@ __device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long l
             b = ls + wp[wf + 1];
         }
         const int64_t first = first_after(P.post, a, b, lx, idmask, lane);
-        if (lane == 0) n_read += (unsigned long long)(le - first);
+        if (lane == 0) ct.read += (uint32_t)(le - first);
         // pass 1: count the matches; pass 2: write them
         int cnt = 0;
         int64_t dst = 0;
@@ -372,13 +396,13 @@ __device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long l
                     bool m = false;
                     float sc = 0.f;
                     if (p < le && (uint32_t)e[u].x >= smin_tag) {
-                        if (pass == 0) { n_visits++; n_cand++; }
+                        if (pass == 0) { ct.visits++; ct.cand++; }
                         sc = xv * __int_as_float(e[u].y);
                         if (sc >= t + beta) {
                             m = true;
                         } else if (sc > t - beta) {  // inside the band: the exact product decides
                             const double ex = (double)xv * (double)__int_as_float(e[u].y);
-                            if (pass == 0) n_band++;
+                            if (pass == 0) ct.band++;
                             m = ex >= (double)t;
                             sc = (float)ex;
                         }
@@ -412,7 +436,7 @@ __device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long l
                         S.i = lx;
                         P.segs[qw] = S;
                     }
-                    n_pairs += (unsigned long long)cnt;
+                    ct.pairs += (uint32_t)cnt;
                 }
                 if (!wr) break;  // no room: the host grows the staging buffer and runs again
             }
@@ -420,31 +444,20 @@ __device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long l
     }
 }
 
-// QMODE: external queries against the index (P.qmode = 1); SPLIT: a self-join whose work
-// list may hold dimension-block items (P.iblk). Each is compiled separately, so that the
-// plain self-join carries none of the other paths' state.
-template <bool QMODE, bool SPLIT = false>
-__global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
+// One class of windowed items (G query groups per CTA, G known at compile time so that the
+// group's shared-memory layout is constant offsets): every group takes items from the
+// class's work list until it is empty, with its own work counters (folded into wtot).
+template <bool QMODE, bool SPLIT, int G>
+__device__ __forceinline__ void join_class(const JoinParams &P, const int64_t item_begin, const int64_t item_end,
+                                        unsigned long long *const work, unsigned long long *const wtot,
+                                        const bool f_minsize, const bool f_remscore, const bool f_upper) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const bool f_minsize = !(P.flags & APS_NO_MINSIZE);
-    const bool f_remscore = !(P.flags & APS_NO_REMSCORE);
-    const bool f_upper = !(P.flags & APS_NO_UPPERBOUND);
-    unsigned long long n_visits = 0, n_cand = 0, n_verified = 0, n_band = 0, n_pairs = 0, n_read = 0;
-    // A CTA that finds a class's work list empty moves on to the next class and re-carves
-    // its shared memory for that class's G, so the classes share one launch and one tail.
-    for (int cls = 0; cls < P.ncls; cls++) {
-    const int64_t item_begin = P.cls_begin[cls], item_end = P.cls_begin[cls + 1];
-    if (item_end <= item_begin) continue;
-    const int G = P.cls_G[cls];
-    unsigned long long *const work = P.work + cls;
-    if (!QMODE && G == 0) {  // single-component vectors: one warp each, no shared memory
-        stream_singles(P, work, item_begin, item_end, f_minsize, f_remscore, n_visits, n_cand, n_pairs, n_band, n_read);
-        continue;
-    }
-    const int GT = JOIN_THREADS / G;
+    Ctr ct;
+    constexpr int GT = JOIN_THREADS / G;
     const int g = threadIdx.x / GT, gt = threadIdx.x % GT;
-    const int lane = gt & 31, gw = gt >> 5, NW = GT >> 5;
-    const int WG = JOIN_WMAX / G, RG = JOIN_RMAX / G;
+    const int lane = gt & 31, gw = gt >> 5;
+    constexpr int NW = GT >> 5;
+    constexpr int WG = JOIN_WMAX / G, RG = JOIN_RMAX / G;
     unsigned char *base = smem + (size_t)g * group_bytes(G);
     uint32_t *A = reinterpret_cast<uint32_t *>(base);  // fixed point, units of 2^-30
     uint32_t *pn4s = A + WG;                                        // [WG / 8], 16-byte aligned
@@ -454,7 +467,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     float *c_xv = reinterpret_cast<float *>(c_ch0 + GT + 4);        // [GT]
     float *xtab = c_xv + GT;                                        // [RG]
     int2 *xr = reinterpret_cast<int2 *>(xtab + RG);
-    const int XG = JOIN_XCAP / G;
+    constexpr int XG = JOIN_XCAP / G;
     uint32_t *bm = reinterpret_cast<uint32_t *>(xr + XG);            // [WG / 32]
     int64_t *wsum = reinterpret_cast<int64_t *>(bm + WG / 32);
     int32_t *wcnt = reinterpret_cast<int32_t *>(wsum + 32);
@@ -467,6 +480,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
     if (gt == 0) bc[3] = bc[4] = bc[5] = 0;  // this group's staging slab: base, used, size
 
     for (;;) {
+        ctr_flush(ct, wtot, lane);
         gsync(G, g, GT);  // every thread is done with the previous item's broadcast slots
         if (gt == 0) bc[0] = (int64_t)atomicAdd(work, 1ull) + item_begin;
         gsync(G, g, GT);
@@ -488,6 +502,10 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
         const float mwx = QMODE ? P.qmw[x] : P.mw[x];
         const float t = QMODE ? P.qt : I.t;
         const float beta = fmaxf(1e-5f, (float)(xl + 2) * 1.1920929e-7f);  // (|x|+2) * 2^-23
+        if (gt == 0) {  // what the emit step needs of x, kept in shared memory (not in registers)
+            bc[6] = QMODE ? x * I.nw : I.qwbase + (int64_t)lx * I.nw;  // x's first (x, window) slot
+            bc[7] = QMODE ? x : (int64_t)lx;                           // x's id in the output
+        }
         // no component reaches remscore >= t: x can create no candidate at all
         if (f_remscore ? qs >= xl : xl == 0) continue;
         // A block item walks its share of x's creating components (every nblk-th, from its
@@ -550,7 +568,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     }
                     cnt = (int32_t)(le - ls);
                     st = ls;
-                    if (gw == 0) n_read += (unsigned long long)cnt;
+                    if (gw == 0) ct.read += (uint32_t)cnt;
                 }
                 const int nch = (cnt + 127) >> 7;
                 int nchk;
@@ -568,11 +586,11 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     // the last component with entries whose first chunk is at or before ch
                     const int cc = 31 - __clz(__ballot_sync(0xffffffffu, nch > 0 && ch0 <= ch));
                     if (phase == 0) {
-                        if (lo > 0) walk_chunks_r<true, true>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
-                        else walk_chunks_r<true, false>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
+                        if (lo > 0) walk_chunks_r<true, true>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, ct.visits);
+                        else walk_chunks_r<true, false>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, ct.visits);
                     } else {
-                        if (lo > 0) walk_chunks_r<false, true>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
-                        else walk_chunks_r<false, false>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
+                        if (lo > 0) walk_chunks_r<false, true>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, ct.visits);
+                        else walk_chunks_r<false, false>(ch, che, cc, st, cnt, ch0, xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, ct.visits);
                     }
                 }
                 cp_async_wait_all();  // the window's codes have landed (visible after the barrier)
@@ -597,7 +615,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     }
                     cnt = (int32_t)(le - ls);
                     st = ls;
-                    n_read += (unsigned long long)cnt;  // every entry of the window's list is loaded
+                    ct.read += (uint32_t)cnt;  // every entry of the window's list is loaded
                 }
                 // scan of (chunks, non-empty, non-empty creating) packed in one int64
                 const int64_t nch = (cnt + 127) >> 7;
@@ -645,11 +663,11 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     // four specialisations: creating or updating, first window (ids at or
                     // below x present) or not
                     if (phase == 0) {
-                        if (lo > 0) walk_chunks<true, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
-                        else walk_chunks<true, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
+                        if (lo > 0) walk_chunks<true, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, ct.visits);
+                        else walk_chunks<true, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, ct.visits);
                     } else {
-                        if (lo > 0) walk_chunks<false, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
-                        else walk_chunks<false, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, n_visits);
+                        if (lo > 0) walk_chunks<false, true>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, ct.visits);
+                        else walk_chunks<false, false>(ch, che, cc, c_start, c_cnt, c_ch0, c_xv, P.post, A, bm, smin_tag, idmask, w0, lo, lane, ct.visits);
                     }
                 }
                 cp_async_wait_all();  // the window's codes have landed (visible after the barrier)
@@ -678,7 +696,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                     word = bm[wq + lane];
                     bm[wq + lane] = 0u;
                 }
-                n_cand += (unsigned long long)__popc(word);
+                ct.cand += (uint32_t)__popc(word);
                 if (f_upper || blk >= 0) {
                     // a block item keeps y by Lemma 1 (local pruning): a match scores
                     // A + dot(x, y') >= t, the blocks that created y hold all of A between
@@ -740,7 +758,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                         if (blk >= 0) stage = 4;  // kept by the local test: score decided in float64
                     }
                     if (stage == 2) {  // short prefixes: each lane its own candidate
-                        n_verified++;
+                        ct.verified++;
                         sc = v + dot_prefix(P.crow + yc.x, yc.y, xtab, RG, xr, xs, xrow, xl);
                         stage = 1;
                     }
@@ -758,7 +776,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
 #pragma unroll
                         for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                         if (lane == src) {
-                            n_verified++;
+                            ct.verified++;
                             sc = v + acc;
                             stage = 1;
                         }
@@ -788,7 +806,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
 #pragma unroll
                         for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                         if (lane == src) {
-                            n_band++;
+                            ct.band++;
                             emit = acc >= (double)t;
                             sc = (float)acc;
                         }
@@ -820,7 +838,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                 const int exw = warp_excl_scan_int(cw, lane, &tot);
                 if (lane < NW) wcnt[lane] = exw;
                 if (lane == 0) {
-                    const int64_t qw = QMODE ? x * I.nw + w : I.qwbase + (int64_t)lx * I.nw + w;
+                    const int64_t qw = bc[6] + w;
                     P.cntq[qw] = tot;
                     int64_t b = 0, wr = 0;
                     if (tot > 0) {
@@ -836,12 +854,12 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
                             Segment S;
                             S.src = b;
                             S.cnt = tot;
-                            S.i = QMODE ? (int32_t)x : lx;
+                            S.i = (int32_t)bc[7];
                             P.segs[qw] = S;
                             wr = 1;
                         }
                     }
-                    n_pairs += (unsigned long long)tot;
+                    ct.pairs += (uint32_t)tot;
                     bc[1] = b;
                     bc[2] = wr;
                 }
@@ -855,15 +873,46 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(JoinParams P) {
             __syncwarp();
         }
     }
+    ctr_flush(ct, wtot, lane);
+}
+
+// QMODE: external queries against the index (P.qmode = 1); SPLIT: a self-join whose work
+// list may hold dimension-block items (P.iblk). Each is compiled separately, so that the
+// plain self-join carries none of the other paths' state.
+template <bool QMODE, bool SPLIT = false>
+__global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(const __grid_constant__ JoinParams P) {
+    const bool f_minsize = !(P.flags & APS_NO_MINSIZE);
+    const bool f_remscore = !(P.flags & APS_NO_REMSCORE);
+    const bool f_upper = !(P.flags & APS_NO_UPPERBOUND);
+    // per-warp 64-bit work totals (visits, candidates, verified, pairs, band, entries read)
+    __shared__ unsigned long long wtot_s[NWARPS][6];
+    for (int i = threadIdx.x; i < NWARPS * 6; i += blockDim.x) (&wtot_s[0][0])[i] = 0ull;
+    __syncthreads();
+    unsigned long long *const wtot = wtot_s[threadIdx.x >> 5];
+    // A CTA that finds a class's work list empty moves on to the next class and re-carves
+    // its shared memory for that class's G, so the classes share one launch and one tail.
+    for (int cls = 0; cls < P.ncls; cls++) {
+    const int64_t item_begin = P.cls_begin[cls], item_end = P.cls_begin[cls + 1];
+    if (item_end <= item_begin) continue;
+    const int G = P.cls_G[cls];
+    unsigned long long *const work = P.work + cls;
+    if (!QMODE && G == 0) {  // single-component vectors: one warp each, no shared memory
+        stream_singles(P, work, item_begin, item_end, f_minsize, f_remscore, wtot);
+        continue;
+    }
+    switch (G) {
+        case 1: join_class<QMODE, SPLIT, 1>(P, item_begin, item_end, work, wtot, f_minsize, f_remscore, f_upper); break;
+        case 2: join_class<QMODE, SPLIT, 2>(P, item_begin, item_end, work, wtot, f_minsize, f_remscore, f_upper); break;
+        case 4: join_class<QMODE, SPLIT, 4>(P, item_begin, item_end, work, wtot, f_minsize, f_remscore, f_upper); break;
+        default: join_class<QMODE, SPLIT, 8>(P, item_begin, item_end, work, wtot, f_minsize, f_remscore, f_upper); break;
+    }
     __syncthreads();  // every group is done with this class's layout of shared memory
     }
-    // flush counters (warp-reduce, one atomic per warp)
-    unsigned long long v6[6] = {n_visits, n_cand, n_verified, n_pairs, n_band, n_read};
+    // flush counters: the warps' totals, one global atomic per counter and warp
+    if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-    for (int k = 0; k < 6; k++) {
-        unsigned long long v = v6[k];
-        for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&P.counters[k < 5 ? k : 6], v);
+        for (int k = 0; k < 6; k++)
+            if (wtot[k]) atomicAdd(&P.counters[k < 5 ? k : 6], wtot[k]);
     }
 }
 
