@@ -333,10 +333,12 @@ __device__ __forceinline__ int64_t first_after(const int2 *__restrict__ post, in
 // (y, w) of r's posting list with y after x and |y| >= minsize is a candidate, and its
 // accumulated score xv * w is already its whole score: x has no other component, and
 // dot(x, y') = 0 since r lies in y's indexed part. So no accumulator and no windows: one
-// warp per vector finds the later part of the list, streams it once to count the matches
-// (decided like the windowed path: float32 outside a band of beta around t, float64
-// inside it) and once more to write them, in increasing y, as x's run in its first
-// window's slot, from a staging slab the warp reserves in bulk.
+// warp per vector finds the later part of the list and streams it, deciding each entry
+// like the windowed path (float32 outside a band of beta around t, float64 inside it) and
+// keeping the matches, in increasing y, in the warp's scratch list; they are then copied
+// as x's run in its first window's slot, from a staging slab the warp reserves in bulk.
+// A vector with more matches than the scratch list holds streams its list a second time
+// to write them there directly.
 __device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long long *work, const int64_t item_begin,
                                             const int64_t item_end, const bool f_minsize, const bool f_remscore,
                                             unsigned long long *wtot) {
@@ -344,6 +346,7 @@ __device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long l
     Ctr ct;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t wslab = max((int64_t)32, P.stage_slab / 8);
+    int2 *const elist = P.scratch + ((size_t)blockIdx.x * NWARPS + (threadIdx.x >> 5)) * JOIN_ECAP;
     int64_t sb = 0, su = 0, ss = 0;  // this warp's staging slab: base, used, size
     for (;;) {
         ctr_flush(ct, wtot, lane);
@@ -377,7 +380,8 @@ __device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long l
         }
         const int64_t first = first_after(P.post, a, b, lx, idmask, lane);
         if (lane == 0) ct.read += (uint32_t)(le - first);
-        // pass 1: count the matches; pass 2: write them
+        // pass 0: count the matches, the first JOIN_ECAP into the scratch list; pass 1 (only
+        // when there were more): write them all into the reserved run
         int cnt = 0;
         int64_t dst = 0;
         bool wr = false;
@@ -408,7 +412,12 @@ __device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long l
                         }
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, m);
-                    if (pass == 1 && m) P.stage[dst + k + __popc(bal & lt_mask)] = make_int2(e[u].x & idmask, __float_as_int(sc));
+                    if (m) {
+                        const int at = k + __popc(bal & lt_mask);
+                        const int2 v2 = make_int2(e[u].x & idmask, __float_as_int(sc));
+                        if (pass == 1) P.stage[dst + at] = v2;
+                        else if (at < JOIN_ECAP) elist[at] = v2;
+                    }
                     k += __popc(bal);
                 }
             }
@@ -439,6 +448,11 @@ __device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long l
                     ct.pairs += (uint32_t)cnt;
                 }
                 if (!wr) break;  // no room: the host grows the staging buffer and runs again
+                if (cnt <= JOIN_ECAP) {  // every match is in the scratch list
+                    __syncwarp();
+                    for (int q = lane; q < cnt; q += 32) P.stage[dst + q] = elist[q];
+                    break;
+                }
             }
         }
     }
