@@ -345,7 +345,7 @@ __global__ void k_wptr(const InstDesc *__restrict__ inst, int k, int64_t M, cons
 // (class, decreasing estimated cost) so that the persistent join takes the most expensive
 // queries first (least-loaded-first idea of the vertical algorithm's binning). Classes 0-3
 // are the instance's tile shape (G = 1, 2, 4, 8 query groups per CTA); class 4 holds the
-// vectors with a single component, which the join streams one warp per vector.
+// vectors with one or two components, which the join streams one warp per vector.
 __global__ void k_item_keys(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
                             const int64_t *__restrict__ lptr, const int32_t *__restrict__ vinst,
                             const InstDesc *__restrict__ inst, int64_t N, uint64_t *keys, uint32_t *vals,
@@ -370,7 +370,7 @@ __global__ void k_item_keys(const int64_t *__restrict__ cptr, const int32_t *__r
             const double lists = (double)lsum;
             double cost = lists * later / (double)I.n + later / 8.0 + 32.0;
             uint64_t c = cost >= 4294967295.0 ? 0xffffffffull : (uint64_t)cost;
-            const int cls = b - a == 1 ? 4 : I.G == 1 ? 0 : I.G == 2 ? 1 : I.G == 4 ? 2 : 3;
+            const int cls = b - a <= 2 ? 4 : I.G == 1 ? 0 : I.G == 2 ? 1 : I.G == 4 ? 2 : 3;
             key = ((uint64_t)cls << 32) | (0xffffffffull - c);
             atomicAdd(&class_count[cls], 1ull);
         } else {

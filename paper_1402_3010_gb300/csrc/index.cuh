@@ -42,7 +42,7 @@ constexpr int JOIN_XCAP = 1280;   // x's row kept in shared memory when |x| <= X
 // up to 128 (W/NW = 1280 for every group shape)
 constexpr int JOIN_ECAP = JOIN_WMAX / (JOIN_THREADS / 32) + 128;
 constexpr int JOIN_STAGE_SLAB = 4096;  // staging slots a query group reserves at a time
-constexpr int JOIN_NCLS = 5;           // work-list classes: G = 1, 2, 4, 8 groups per CTA; single-component vectors
+constexpr int JOIN_NCLS = 5;           // work-list classes: G = 1, 2, 4, 8 groups per CTA; vectors of <= 2 components
 // ||y'||_2 bounds in 4 bits per vector: code c stands for c * PN4_STEP (PN4_STEP = 1.01 / 15,
 // above any norm the index accepts), and PN4_UNIT = PN4_STEP in units of 2^-30, rounded up
 constexpr float PN4_STEP = 1.01f / 15.f;
@@ -127,7 +127,7 @@ struct aps_index {
     aps::IndexArrays d;
     // join work list: vectors in decreasing estimated cost, grouped by class
     aps::DBuf<int32_t> items;
-    int64_t class_begin[aps::JOIN_NCLS + 1] = {};  // classes G = 1, 2, 4, 8, then single-component vectors
+    int64_t class_begin[aps::JOIN_NCLS + 1] = {};  // classes G = 1, 2, 4, 8, then vectors of <= 2 components
     // output sizing from the previous join
     int64_t hint_pairs = 0;
     // pairs per query (times 16) that query batches on this index have needed at most: the

@@ -46,7 +46,7 @@ struct JoinParams {
     const int32_t *items;
     // classes, taken in order by one persistent launch: class c is the work-list range
     // [cls_begin[c], cls_begin[c + 1]) run with cls_G[c] query groups per CTA, or, when
-    // cls_G[c] is 0, one warp per single-component vector
+    // cls_G[c] is 0, one warp per vector with one or two components
     int ncls;
     int cls_G[JOIN_NCLS];
     int64_t cls_begin[JOIN_NCLS + 1];
@@ -329,19 +329,59 @@ __device__ __forceinline__ int64_t first_after(const int2 *__restrict__ post, in
     return m ? a + (__ffs(m) - 1) : b;
 }
 
-// The vectors with a single component r (value xv) (Alg. 2 for |x| = 1). Every entry
-// (y, w) of r's posting list with y after x and |y| >= minsize is a candidate, and its
-// accumulated score xv * w is already its whole score: x has no other component, and
-// dot(x, y') = 0 since r lies in y's indexed part. So no accumulator and no windows: one
-// warp per vector finds the later part of the list and streams it, deciding each entry
-// like the windowed path (float32 outside a band of beta around t, float64 inside it) and
-// keeping the matches, in increasing y, in the warp's scratch list; they are then copied
-// as x's run in its first window's slot, from a staging slab the warp reserves in bulk.
-// A vector with more matches than the scratch list holds streams its list a second time
-// to write them there directly.
-__device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long long *work, const int64_t item_begin,
-                                            const int64_t item_end, const bool f_minsize, const bool f_remscore,
-                                            unsigned long long *wtot) {
+// The part of a posting list after x: [first, end) of list rank r of instance I (the
+// search starts in the window of x's successor, whose part of the list holds the answer
+// or ends right before it).
+__device__ __forceinline__ void list_after(const JoinParams &P, const InstDesc &I, const int r, const int32_t lx,
+                                           const int wf, const int32_t idmask, const int lane, int64_t &first,
+                                           int64_t &end) {
+    const int64_t R = (int64_t)I.rbase + r;
+    const int64_t ls = P.lptr[R];
+    end = P.lptr[R + 1];
+    int64_t a = ls, b = end;
+    if (I.nw > 1) {
+        const int32_t *wp = P.wptr + I.wbase + (int64_t)r * (I.nw + 1);
+        a = ls + wp[wf];
+        b = ls + wp[wf + 1];
+    }
+    first = first_after(P.post, a, b, lx, idmask, lane);
+}
+
+// Number of the 32 values v held by the lanes (increasing with the lane, padded with
+// INT_MAX) that are below key (LE: at or below key), by halving over the lanes.
+template <bool LE>
+__device__ __forceinline__ int count_below(const int v, const int key) {
+    int c = 0;
+#pragma unroll
+    for (int h = 16; h; h >>= 1) {
+        const int w = __shfl_sync(0xffffffffu, v, c + h - 1);
+        if (LE ? w <= key : w < key) c += h;
+    }
+    const int w = __shfl_sync(0xffffffffu, v, 31);
+    if (c == 31 && (LE ? w <= key : w < key)) c = 32;
+    return c;
+}
+
+// The vectors with one or two components (Alg. 2 for |x| <= 2), one warp per vector, no
+// accumulator and no windows.
+//   |x| = 1 (rank r, value x0): every entry (y, w) of r's list with y after x and
+//   |y| >= minsize is a candidate whose accumulated score x0 * w is its whole score (x has
+//   no other component, and dot(x, y') = 0 since r lies in y's indexed part).
+//   |x| = 2 (ranks r0 < r1, values x0, x1): the two lists after x are merged by id, 32
+//   entries at a time. An id on both lists scores x0 * w0 + x1 * w1 (both ranks in y's
+//   indexed part, so y's prefix holds neither); an id on r0's list alone scores x0 * w0
+//   (y has no r1: it is not in the indexed part, and the prefix ranks lie below r0), and is
+//   a candidate only if r0 may create (remscore); an id on r1's list alone scores
+//   x1 * w1 + x0 * y[r0], where y[r0] can only sit in y's unindexed prefix (looked up there
+//   unless the ||y'||_2 bound already rules the pair out).
+// Each candidate is decided like the windowed path (float32 outside a band of beta around
+// t, the exact float64 sum of the products inside it). The matches, in increasing y, go to
+// the warp's scratch list and are then copied as x's run in its first window's slot, from
+// a staging slab the warp reserves in bulk; a vector with more matches than the scratch
+// list holds is streamed a second time, writing them there directly.
+__device__ __forceinline__ void stream_short(const JoinParams &P, unsigned long long *work, const int64_t item_begin,
+                                          const int64_t item_end, const bool f_minsize, const bool f_remscore,
+                                          unsigned long long *wtot) {
     const int lane = threadIdx.x & 31;
     Ctr ct;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -358,67 +398,167 @@ __device__ __noinline__ void stream_singles(const JoinParams &P, unsigned long l
         const InstDesc I = P.inst[P.vinst[x]];
         const int32_t lx = (int32_t)(x - I.vbase);
         const int4 xm = P.vmeta[x];
-        if (f_remscore && P.qsplit[x] >= xm.y) continue;  // remscore < t: no candidate at all
-        const int2 xe = P.crow[xm.x];
-        const float xv = __int_as_float(xe.y);
+        const int xl = xm.y;  // 1 or 2
+        const int qs = f_remscore ? P.qsplit[x] : 0;
+        if (qs >= xl) continue;  // remscore < t from the first component on: no candidate
+        const int2 xe0 = P.crow[xm.x];
+        const int2 xe1 = xl == 2 ? P.crow[xm.x + 1] : make_int2(0, 0);
+        const float x0 = __int_as_float(xe0.y), x1 = __int_as_float(xe1.y);
         const float t = I.t;
-        const float beta = fmaxf(1e-5f, 3.f * 1.1920929e-7f);  // (|x| + 2) * 2^-23 with |x| = 1
+        const float beta = fmaxf(1e-5f, (float)(xl + 2) * 1.1920929e-7f);  // (|x| + 2) * 2^-23
         const float mwx = P.mw[x];
         int smin = 0;  // minsize, bounded as in the windowed path
         if (f_minsize && I.packed && mwx > 0.f)
             smin = (int)ceilf(fminf(__fdiv_rd(__fsub_rd(t, beta), __fmul_ru(mwx, 1.0020001f)), 255.f));
         const uint32_t smin_tag = (uint32_t)max(smin, 0) << 24;
         const int32_t idmask = I.packed ? 0x00ffffff : 0x7fffffff;
-        const int64_t R = (int64_t)I.rbase + xe.x;
-        const int64_t ls = P.lptr[R], le = P.lptr[R + 1];
         const int wf = (lx + 1) / I.W;  // the window of x's successor
-        int64_t a = ls, b = le;
-        if (I.nw > 1) {  // the answer lies in that window's part of the list, or right after it
-            const int32_t *wp = P.wptr + I.wbase + (int64_t)xe.x * (I.nw + 1);
-            a = ls + wp[wf];
-            b = ls + wp[wf + 1];
-        }
-        const int64_t first = first_after(P.post, a, b, lx, idmask, lane);
-        if (lane == 0) ct.read += (uint32_t)(le - first);
+        int64_t f0, e0, f1 = 0, e1 = 0;
+        list_after(P, I, xe0.x, lx, wf, idmask, lane, f0, e0);
+        if (xl == 2) list_after(P, I, xe1.x, lx, wf, idmask, lane, f1, e1);
+        if (lane == 0) ct.read += (uint32_t)((e0 - f0) + (e1 - f1));
         // pass 0: count the matches, the first JOIN_ECAP into the scratch list; pass 1 (only
         // when there were more): write them all into the reserved run
         int cnt = 0;
         int64_t dst = 0;
         bool wr = false;
         for (int pass = 0; pass < 2; pass++) {
-            int k = 0;  // matches written so far
-            for (int64_t p0 = first; p0 < le; p0 += 128) {
-                int2 e[4];
+            int k = 0;  // matches so far
+            if (xl == 1) {
+                for (int64_t p0 = f0; p0 < e0; p0 += 128) {
+                    int2 e[4];
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int64_t p = p0 + u * 32 + lane;
-                    e[u] = p < le ? __ldg(&P.post[p]) : make_int2(0, 0);
+                    for (int u = 0; u < 4; u++) {
+                        const int64_t p = p0 + u * 32 + lane;
+                        e[u] = p < e0 ? __ldg(&P.post[p]) : make_int2(0, 0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int64_t p = p0 + u * 32 + lane;
+                        bool m = false;
+                        float sc = 0.f;
+                        if (p < e0 && (uint32_t)e[u].x >= smin_tag) {
+                            if (pass == 0) { ct.visits++; ct.cand++; }
+                            sc = x0 * __int_as_float(e[u].y);
+                            if (sc >= t + beta) {
+                                m = true;
+                            } else if (sc > t - beta) {  // inside the band: the exact product decides
+                                const double ex = (double)x0 * (double)__int_as_float(e[u].y);
+                                if (pass == 0) ct.band++;
+                                m = ex >= (double)t;
+                                sc = (float)ex;
+                            }
+                        }
+                        const unsigned bal = __ballot_sync(0xffffffffu, m);
+                        if (m) {
+                            const int at = k + __popc(bal & lt_mask);
+                            const int2 v2 = make_int2(e[u].x & idmask, __float_as_int(sc));
+                            if (pass == 1) P.stage[dst + at] = v2;
+                            else if (at < JOIN_ECAP) elist[at] = v2;
+                        }
+                        k += __popc(bal);
+                    }
                 }
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int64_t p = p0 + u * 32 + lane;
-                    bool m = false;
-                    float sc = 0.f;
-                    if (p < le && (uint32_t)e[u].x >= smin_tag) {
-                        if (pass == 0) { ct.visits++; ct.cand++; }
-                        sc = xv * __int_as_float(e[u].y);
-                        if (sc >= t + beta) {
-                            m = true;
-                        } else if (sc > t - beta) {  // inside the band: the exact product decides
-                            const double ex = (double)xv * (double)__int_as_float(e[u].y);
-                            if (pass == 0) ct.band++;
-                            m = ex >= (double)t;
-                            sc = (float)ex;
+            } else {
+                // merge of the two lists after x, 32 merged entries per step: lane l holds
+                // entry i + l of r0's list (a) and entry j + l of r1's list (b); an entry's
+                // place in the merged order is its lane plus the other list's entries below
+                // it (ties: a first, so an id on both lists gives a then b, adjacent)
+                const int64_t n0 = e0 - f0, n1 = e1 - f1;
+                int64_t i = 0, j = 0;
+                const bool create0 = qs == 0;  // r0 may create candidates (remscore >= t)
+                while (i < n0 || j < n1) {
+                    const bool va = i + lane < n0, vb = j + lane < n1;
+                    const int2 ea = va ? __ldg(&P.post[f0 + i + lane]) : make_int2(0x7fffffff, 0);
+                    const int2 eb = vb ? __ldg(&P.post[f1 + j + lane]) : make_int2(0x7fffffff, 0);
+                    const int ida = va ? (ea.x & idmask) : 0x7fffffff;
+                    const int idb = vb ? (eb.x & idmask) : 0x7fffffff;
+                    const int nb = count_below<false>(idb, ida);  // b entries below a
+                    const int na = count_below<true>(ida, idb);   // a entries at or below b
+                    const int ra = lane + nb, rb = lane + na;       // places in the merged order
+                    const bool ina = va && ra < 32, inb = vb && rb < 32;
+                    const float wbd = __int_as_float(__shfl_sync(0xffffffffu, eb.y, nb & 31));
+                    // (every lane takes part in the shuffles; their results are used where valid)
+                    const int idb_nb = __shfl_sync(0xffffffffu, idb, nb & 31);
+                    const int ida_na = __shfl_sync(0xffffffffu, ida, (na - 1) & 31);
+                    const bool dupa = va && nb < 32 && idb_nb == ida;
+                    const bool dupb = vb && na > 0 && ida_na == idb;
+                    const int ca = __popc(__ballot_sync(0xffffffffu, ina));
+                    int cb = __popc(__ballot_sync(0xffffffffu, inb));
+                    // an id on both lists whose a entry closes the step: its b entry goes too
+                    {
+                        const bool nd = __shfl_sync(0xffffffffu, dupb, cb & 31), nv2 = __shfl_sync(0xffffffffu, vb, cb & 31);
+                        const int nna = __shfl_sync(0xffffffffu, na, cb & 31);
+                        if (cb < 32 && nv2 && nd && nna <= ca) cb++;
+                    }
+                    // candidates: a entries (on both lists, or r0 may create), b entries alone
+                    bool ma = false, mb = false;
+                    float sa = 0.f, sbs = 0.f;
+                    if (ina && (uint32_t)ea.x >= smin_tag) {
+                        if (pass == 0) ct.visits += dupa ? 2u : 1u;  // the b entry of a shared id visits too
+                        if (dupa || create0) {
+                            if (pass == 0) ct.cand++;
+                            const float wa = __int_as_float(ea.y), wb = dupa ? wbd : 0.f;
+                            sa = fmaf(x1, wb, x0 * wa);
+                            if (sa >= t + beta) {
+                                ma = true;
+                            } else if (sa > t - beta) {
+                                const double ex = (double)x0 * (double)wa + (double)x1 * (double)wb;
+                                if (pass == 0) ct.band++;
+                                ma = ex >= (double)t;
+                                sa = (float)ex;
+                            }
                         }
                     }
-                    const unsigned bal = __ballot_sync(0xffffffffu, m);
-                    if (m) {
-                        const int at = k + __popc(bal & lt_mask);
-                        const int2 v2 = make_int2(e[u].x & idmask, __float_as_int(sc));
+                    if (inb && !dupb && (uint32_t)eb.x >= smin_tag) {
+                        if (pass == 0) { ct.visits++; ct.cand++; }
+                        const float wb = __int_as_float(eb.y);
+                        const float s1 = x1 * wb;
+                        float y0 = 0.f;
+                        // y[r0] <= 1 + 1e-3 (the norm tolerance): most pairs stop here, unloaded
+                        bool look = s1 + x0 * 1.0011f > t - beta;
+                        int4 yc = make_int4(0, 0, 0, 0);  // {row offset, |y'|, ., ||y'||_2 bound}
+                        if (look) {
+                            yc = __ldg(&P.vcand[I.vbase + idb]);
+                            look = yc.y > 0 && s1 + x0 * __int_as_float(yc.w) > t - beta;
+                        }
+                        if (look) {  // r0 in y's unindexed prefix (ranks increasing)?
+                            if (pass == 0) ct.verified++;
+                            for (int q = 0; q < yc.y; q++) {
+                                const int2 ye = __ldg(&P.crow[yc.x + q]);
+                                if (ye.x >= xe0.x) {
+                                    if (ye.x == xe0.x) y0 = __int_as_float(ye.y);
+                                    break;
+                                }
+                            }
+                        }
+                        sbs = fmaf(x0, y0, s1);
+                        if (sbs >= t + beta) {
+                            mb = true;
+                        } else if (sbs > t - beta) {
+                            const double ex = (double)x0 * (double)y0 + (double)x1 * (double)wb;
+                            if (pass == 0) ct.band++;
+                            mb = ex >= (double)t;
+                            sbs = (float)ex;
+                        }
+                    }
+                    // matches in merged order: a bit per place
+                    const unsigned mm = __reduce_or_sync(0xffffffffu, (ma ? 1u << ra : 0u) | (mb ? 1u << rb : 0u));
+                    if (ma) {  // (a lane may hold a match in both lists)
+                        const int at = k + __popc(mm & ((1u << ra) - 1u));
+                        const int2 v2 = make_int2(ida, __float_as_int(sa));
                         if (pass == 1) P.stage[dst + at] = v2;
                         else if (at < JOIN_ECAP) elist[at] = v2;
                     }
-                    k += __popc(bal);
+                    if (mb) {
+                        const int at = k + __popc(mm & ((1u << rb) - 1u));
+                        const int2 v2 = make_int2(idb, __float_as_int(sbs));
+                        if (pass == 1) P.stage[dst + at] = v2;
+                        else if (at < JOIN_ECAP) elist[at] = v2;
+                    }
+                    k += __popc(mm);
+                    i += ca;
+                    j += cb;
                 }
             }
             if (pass == 0) {
@@ -910,8 +1050,8 @@ __global__ void __launch_bounds__(JOIN_THREADS, 1) join_kernel(const __grid_cons
     if (item_end <= item_begin) continue;
     const int G = P.cls_G[cls];
     unsigned long long *const work = P.work + cls;
-    if (!QMODE && G == 0) {  // single-component vectors: one warp each, no shared memory
-        stream_singles(P, work, item_begin, item_end, f_minsize, f_remscore, wtot);
+    if (!QMODE && G == 0) {  // vectors with one or two components: one warp each, no shared memory
+        stream_short(P, work, item_begin, item_end, f_minsize, f_remscore, wtot);
         continue;
     }
     switch (G) {
@@ -957,7 +1097,7 @@ __global__ void k_inst_offsets(const InstDesc *__restrict__ inst, int k, const i
 }
 
 // The index's work-list classes as one launch's class list. Returns the CTA count (enough
-// for every class's groups, or warps for the single-component class, at most max_ctas) and
+// for every class's groups, or warps for the class of one- and two-component vectors, at most max_ctas) and
 // sets *smem to the largest class layout used.
 int set_classes(JoinParams &P, const aps_index *ix, int max_ctas, int *smem) {
     static const int Gs[JOIN_NCLS] = {1, 2, 4, 8, 0};
@@ -1105,7 +1245,7 @@ __global__ void k_split_place(const unsigned long long *__restrict__ key, const 
 }  // namespace
 
 // Staging slots one CTA can reserve and leave unused: a slab per group of every windowed
-// class (1 + 2 + 4 + 8 groups) and a slab per warp of the single-component class.
+// class (1 + 2 + 4 + 8 groups) and a slab per warp of the streamed class.
 int64_t join_slab_slack() { return 15 * (int64_t)JOIN_STAGE_SLAB + (int64_t)NWARPS * (JOIN_STAGE_SLAB / 8); }
 
 void debug_stage_cap(int64_t pairs) { g_stage_cap_once.store(pairs > 0 ? pairs : 0); }
@@ -1139,7 +1279,7 @@ aps_status join_all_pairs(aps_index *ix, uint32_t flags, aps_pairs *out, std::ve
     DBuf<uint32_t> sp_score;
     if (split) {
         // block items come from the windowed classes (G = 1 ... 8), never from the
-        // single-component class that follows them
+        // streamed class (one- and two-component vectors) that follows them
         for (int c = 0; c < 4; c++)
             if (ix->class_begin[c + 1] > ix->class_begin[c]) split_cls = c;
         const int64_t nitems = ix->class_begin[JOIN_NCLS] - ix->class_begin[0];
