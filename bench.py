@@ -589,7 +589,40 @@ def run_dense(args, rank, world):
         finally:
             aps.aps_pairs_free(p)
         line["precision_vs_fp64"] = dense_precision(X, t, rows, gi, gj, gs, ref)
+        line["accumulation_error"] = dense_accumulation(aps)
     return line
+
+
+def bf16_round(X):
+    """float32 -> the nearest BF16 value (ties to even), as float64 (finite inputs)."""
+    b = np.ascontiguousarray(X, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def dense_accumulation(aps, n=4096):
+    """The tensor cores' float32 accumulation error, which the dense margin bounds by
+    2d * 2^-23: max |S_tc - S_fp64| over every computed entry of a 4096-row mixture (64
+    clusters, products up to ~1), S_fp64 the float64 product of the same BF16-rounded rows."""
+    import torch
+
+    import synth
+
+    out = {}
+    for d in (256, 512):
+        X = synth.dense_mixture(n, d, 64, 0.05, seed=11).astype(np.float32)
+        raw = torch.full((n, n), float("nan"), device="cuda")
+        aps.aps_dense_tensor_products(torch.from_numpy(X).cuda(), raw)
+        S = raw.cpu().numpy().astype(np.float64)
+        del raw
+        Xb = bf16_round(X)
+        blk = np.arange(n) // 256
+        computed = blk[None, :] >= blk[:, None]
+        err = np.abs(S - Xb @ Xb.T)[computed]
+        bound = 2 * d * 2.0 ** -23
+        out[f"d{d}"] = {"max_abs": float(err.max()), "mean_abs": float(err.mean()), "bound_2d_2^-23": bound,
+                        "max_over_bound": float(err.max() / bound), "entries": int(computed.sum())}
+    return out
 
 
 def dense_precision(X, t, rows, gi, gj, gs, ref, band=1e-5):

@@ -326,6 +326,15 @@ aps_status aps_autotune_batch_csr(int32_t k, const int64_t *row_offsets, const i
  * usable), APS_ENOMEM, APS_ECUDA; *out is then empty. */
 aps_status aps_all_pairs_dense(const float *X, int32_t n, int32_t d, float t, uint32_t flags,
                                void *stream, aps_pairs *out, aps_stats *stats);
+/* Measurement of the dense path's arithmetic: the float32 products S_ij = X_bf16,i . X_bf16,j
+ * exactly as aps_all_pairs_dense's tensor-core kernel accumulates them (X rounded to BF16,
+ * products summed in float32 in the tensor memory), written to raw[i * n + j] for every
+ * computed entry: the 256-row blocks on and above the block diagonal (j's block >= i's
+ * block); other entries are left as they were. X (n x d float32, row-major, 16-byte
+ * aligned) and raw (n * n float32) are device pointers owned by the caller; rows are taken
+ * as they are (no norm check). d as in aps_all_pairs_dense; n <= 16384. Synchronizes
+ * stream. Errors: APS_EINVAL, APS_EUNSUPPORTED, APS_ETIMEOUT, APS_ENOMEM, APS_ECUDA. */
+aps_status aps_dense_tensor_products(const float *X, int32_t n, int32_t d, float *raw, void *stream);
 
 /* ---- the similarity graph -------------------------------------------------------- */
 /* CSR adjacency of G_S (Sec. 2.1) from a pair list: each pair (i[p], j[p], s[p]) gives the

@@ -18,7 +18,8 @@ __all__ = [
     "aps_build_index", "aps_all_pairs", "aps_query", "aps_index_export", "aps_index_info",
     "aps_index_stats", "aps_index_free", "aps_pairs_free", "aps_pairs_copy_to",
     "aps_batch_all_pairs", "aps_batch_all_pairs_csr", "aps_tune_bucket", "aps_tuning_default", "aps_get_tuning",
-    "aps_set_tuning", "aps_autotune_batch_csr", "aps_all_pairs_dense", "aps_server_create", "aps_stream_submit",
+    "aps_set_tuning", "aps_autotune_batch_csr", "aps_all_pairs_dense", "aps_dense_tensor_products",
+    "aps_server_create", "aps_stream_submit",
     "aps_stream_poll", "aps_stream_cancel", "aps_server_free", "aps_last_error", "aps_version",
     "aps_debug_fail_alloc", "aps_debug_dense_stall", "aps_debug_stage_cap", "aps_launch_count",
     "aps_all_pairs_noalloc", "pairs_to_numpy", "pairs_to_torch",
@@ -164,6 +165,7 @@ def load():
                                               ctypes.POINTER(aps_tune_report)]),
             "aps_batch_all_pairs_csr": (_i32, [_i32, _P, _P, _P, _P, _P, _P, _u32, _P, ctypes.POINTER(aps_pairs),
                                                ctypes.POINTER(aps_stats)]),
+            "aps_dense_tensor_products": (_i32, [_P, _i32, _i32, _P, _P]),
             "aps_all_pairs_dense": (_i32, [_P, _i32, _i32, _f32, _u32, _P, ctypes.POINTER(aps_pairs),
                                            ctypes.POINTER(aps_stats)]),
             "aps_server_create": (_i32, [_P, ctypes.c_size_t, _i32, ctypes.POINTER(_P)]),
@@ -506,6 +508,19 @@ def aps_all_pairs_dense(X, t: float, flags: int = 0, stream=None):
     _check(lib.aps_all_pairs_dense(ptr, int(n), int(d), float(t), int(flags) | f, _stream_ptr(stream),
                                    ctypes.byref(out), ctypes.byref(st)), "aps_all_pairs_dense")
     return out, st.as_dict()
+
+
+def aps_dense_tensor_products(X, raw, stream=None) -> None:
+    """X: contiguous CUDA float32 [n, d]; raw: contiguous CUDA float32 [n, n], receiving the
+    tensor cores' float32 products of the dense path's computed blocks."""
+    for a in (X, raw):
+        if not _is_torch(a) or not a.is_cuda or str(a.dtype) != "torch.float32" or not a.is_contiguous():
+            raise TypeError("X and raw must be contiguous CUDA float32 tensors")
+    n, d = X.shape
+    if tuple(raw.shape) != (n, n):
+        raise ValueError("raw must be n x n")
+    _check(load().aps_dense_tensor_products(X.data_ptr(), int(n), int(d), raw.data_ptr(), _stream_ptr(stream)),
+           "aps_dense_tensor_products")
 
 
 def aps_server_create(index: int, mem_budget: int, slots: int) -> int:

@@ -570,6 +570,23 @@ aps_status aps_all_pairs_dense(const float *X, int32_t n, int32_t d, float t, ui
     return st;
 }
 
+aps_status aps_dense_tensor_products(const float *X, int32_t n, int32_t d, float *raw, void *stream) {
+    if (n < 0 || n > 16384 || d < 64 || d > 512 || d % 64 != 0 || (n > 0 && (!X || !raw))) {
+        set_error("need 0 <= n <= 16384, device X and raw, and d a multiple of 64 in [64, 512] (got n=%d d=%d)", n,
+                  d);
+        return APS_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(X) & 15) {
+        set_error("X must be 16-byte aligned");
+        return APS_EINVAL;
+    }
+    if (n == 0) return APS_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    APS_TRY(dense_tensor_products(X, n, d, s, raw));
+    APS_CUDA(cudaStreamSynchronize(s));
+    return APS_OK;
+}
+
 const char *aps_version(void) { return "aps 0.1 (sm_103a)"; }
 
 void aps_debug_fail_alloc(int64_t k) { set_alloc_fault(k); }

@@ -58,6 +58,7 @@ struct DenseParams {
     unsigned long long wait_ns;  // time limit of one mbarrier wait
     uint32_t stall;              // test hook: 1 = the MMA issuer waits for an accumulator release
                                  // that never comes, so the waits run out
+    float *raw;                  // measurement: when set, every computed product S_ij (row-major n x n)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -449,6 +450,11 @@ __global__ void __launch_bounds__(DN_THREADS, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive_cluster(map_to_rank(&d_empty[buf], 0));
+                if (P.raw && i < P.n) {  // (measurement only) this thread's row slice of the products
+                    const int jb = bc * PAIR_ROWS + h * EPI_COLS;
+                    for (int kk = 0; kk < EPI_COLS; kk++)
+                        if (jb + kk < P.n) P.raw[(int64_t)i * P.n + jb + kk] = __uint_as_float(r[kk]);
+                }
                 for (int cc = 0; cc < EPI_COLS / 64; cc++) {
                     const int j0 = bc * PAIR_ROWS + h * EPI_COLS + cc * 64;
                     unsigned long long m = 0ull;
@@ -657,7 +663,7 @@ double dense_margin(int d) {
 }
 
 aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t, cudaStream_t s, aps_pairs *out,
-                                  aps_stats *stats) {
+                                  aps_stats *stats, float *raw) {
     int dev = 0, major = 0, minor = 0;
     APS_CUDA(cudaGetDevice(&dev));
     APS_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
@@ -738,7 +744,7 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
         P.S = S;
         P.nunits = (int)units.size();
         P.units = dunits.p;
-        P.thr = (float)((double)t - delta);
+        P.thr = raw ? INFINITY : (float)((double)t - delta);
         P.cand = cand.p;
         P.cap = (unsigned long long)cap;
         P.count = ctr.p;
@@ -746,6 +752,7 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
         P.err = err.p;
         P.wait_ns = WAIT_NS_DEFAULT;
         P.stall = 0;
+        P.raw = raw;
         for (int64_t k = g_dense_stall.load(); k > 0;)
             if (g_dense_stall.compare_exchange_weak(k, k - 1)) {
                 P.stall = 1;
@@ -779,6 +786,10 @@ aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t,
             return APS_ETIMEOUT;
         }
         cudaEventElapsedTime(&ms_gemm, ev[1], ev[2]);
+        if (raw) {  // the products are written: no candidates to finish
+            out->count = 0;
+            return APS_OK;
+        }
         nslots = (int64_t)cnt[0];
         npad = (int64_t)cnt[2];
         if (nslots <= cap) break;
@@ -885,7 +896,16 @@ aps_status dense_all_pairs(const float *X, int32_t n, int32_t d, float t, uint32
                   b);
         return APS_EINVAL;
     }
-    return dense_all_pairs_device(norm ? dy.p : Xd, n, d, t, s, out, stats);
+    return dense_all_pairs_device(norm ? dy.p : Xd, n, d, t, s, out, stats, nullptr);
+}
+
+// The tensor cores' float32 products S = X_bf16 . X_bf16^T of the dense path (rows as they
+// are, no validation), each computed entry written to raw (row-major n x n); entries of
+// 256-row blocks below the diagonal are not computed and left as they were.
+aps_status dense_tensor_products(const float *X, int32_t n, int32_t d, cudaStream_t s, float *raw) {
+    aps_pairs none;
+    memset(&none, 0, sizeof(none));
+    return dense_all_pairs_device(X, n, d, 0.f, s, &none, nullptr, raw);
 }
 
 }  // namespace aps

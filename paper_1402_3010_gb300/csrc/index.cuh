@@ -211,7 +211,10 @@ aps_status join_noalloc(aps_index *ix, unsigned char *arena, size_t arena_bytes,
 aps_status dense_all_pairs(const float *X, int32_t n, int32_t d, float t, uint32_t flags, cudaStream_t s,
                            aps_pairs *out, aps_stats *stats);
 aps_status dense_all_pairs_device(const float *X, int32_t n, int32_t d, float t, cudaStream_t s, aps_pairs *out,
-                                  aps_stats *stats);
+                                  aps_stats *stats, float *raw);
+// The tensor cores' float32 products X_bf16 . X_bf16^T of the computed (upper) blocks into
+// raw (row-major n x n, device memory); X on the device.
+aps_status dense_tensor_products(const float *X, int32_t n, int32_t d, cudaStream_t s, float *raw);
 double dense_margin(int d);
 void dense_debug_stall(int64_t launches, uint64_t wait_ns);
 void debug_stage_cap(int64_t pairs);

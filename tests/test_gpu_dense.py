@@ -172,3 +172,37 @@ def test_dense_wait_limit_expires_and_context_stays_usable(aps, n, d, wait_ns):
     if n <= 2000:
         ref = oracle.dense_all_pairs(X, f32(t))
         assert compare(after[0], after[1], after[2], ref, f32(t), n, dense=X)["pairs"] > 0
+
+
+def bf16_round(X):
+    """float32 -> the nearest BF16 value (ties to even), as float64 (finite inputs)."""
+    b = np.ascontiguousarray(X, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("d", [256, 512])
+def test_tensor_products_accumulation_error_within_margin(aps, d):
+    """The dense margin delta = (2u + u^2) * 1.002 + 2d * 2^-23 assumes the tensor cores'
+    float32 accumulation of the BF16 products errs by at most 2d * 2^-23 on unit rows
+    (Sec. 2.1, S = D.D^T). Measured here against the exact (float64) product of the same
+    BF16-rounded rows, over every computed entry of a 4096-row mixture with many near-
+    duplicate rows (products near 1, the largest sums)."""
+    import torch
+
+    n = 4096
+    X = synth.dense_mixture(n, d, 64, 0.05, seed=11).astype(np.float32)
+    raw = torch.full((n, n), float("nan"), device="cuda")
+    aps.aps_dense_tensor_products(torch.from_numpy(X).cuda(), raw)
+    S = raw.cpu().numpy().astype(np.float64)
+    Xb = bf16_round(X)
+    S64 = Xb @ Xb.T
+    blk = np.arange(n) // 256
+    computed = blk[None, :] >= blk[:, None]
+    assert np.isfinite(S[computed]).all() and np.isnan(S[~computed]).all()
+    err = np.abs(S[computed] - S64[computed])
+    bound = 2 * d * 2.0 ** -23
+    assert err.max() <= bound, f"max accumulation error {err.max():.3e} > 2d * 2^-23 = {bound:.3e}"
+    # the products are of BF16-rounded rows: their distance to the float32 rows' products is
+    # the rounding part of delta, not the accumulation part
+    assert np.abs(S64[computed]).max() <= 1.0 + 1e-2
