@@ -34,9 +34,11 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 // ------------------------------------------------------------------ memory
 static std::mutex g_pool_mu;
 static bool g_pool_ready[64];
-static int64_t g_alloc_fault = 0;
+// test hook: the k-th device allocation from now fails (atomic: serving slots allocate
+// from their own threads)
+static std::atomic<int64_t> g_alloc_fault{0};
 
-void set_alloc_fault(int64_t k) { g_alloc_fault = k; }
+void set_alloc_fault(int64_t k) { g_alloc_fault.store(k); }
 
 static void pool_setup() {
     int dev = 0;
@@ -53,7 +55,7 @@ static void pool_setup() {
 
 aps_status dalloc(void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
-    if (g_alloc_fault > 0 && --g_alloc_fault == 0) {
+    if (g_alloc_fault.load() > 0 && g_alloc_fault.fetch_sub(1) == 1) {
         set_error("device allocation of %zu bytes failed (injected)", bytes);
         return APS_ENOMEM;
     }
