@@ -355,7 +355,7 @@ def run_aps(args, rank, world):
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if args.e2e_steps > 0:
-        time.sleep(1.0)  # let the stopped clock sampler's driver session wind down first
+        time.sleep(3.0)  # let the stopped clock sampler's driver session wind down first
         pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
         hip, hix, hvv = pin(c.indptr), pin(c.idx), pin(c.val)
         npairs = cnt
@@ -378,7 +378,7 @@ def run_aps(args, rank, world):
             aps.aps_index_free(h)
             return n_out
 
-        for _ in range(2):
+        for _ in range(3):
             e2e_step()
         del gpu_ms[:]
         barrier()
@@ -1084,7 +1084,7 @@ def run_split(args):
 
 FORM_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "dtype", "config", "roofline", "latency_ms", "split",
              "phases_ms", "work", "serving", "tiles", "clocks", "cpu_baseline", "accuracy", "precision_vs_fp64",
-             "e2e", "gpu_launches", "gpu_launches_unit")
+             "accumulation_error", "e2e", "gpu_launches", "gpu_launches_unit")
 
 
 def as_form(line):

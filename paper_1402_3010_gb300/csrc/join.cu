@@ -263,20 +263,6 @@ __device__ __forceinline__ void walk_chunks(int ch, const int che, int cc, const
     n_visits += nv;
 }
 
-// In x's first window, the first entry of [ls, le) after x (ids increase along a list), by
-// bisection. Taken for long segments only (at least SKIP_MIN entries), where the entries at
-// or before x that it skips outweigh its dependent loads.
-constexpr int64_t SKIP_MIN = 128;
-__device__ __forceinline__ int64_t first_after_x(const int2 *__restrict__ post, int64_t ls, const int64_t le,
-                                                 const int32_t lx, const int32_t idmask) {
-    int64_t hi = le;
-    while (ls < hi) {
-        const int64_t mid = (ls + hi) >> 1;
-        if ((__ldg(&post[mid].x) & idmask) > lx) hi = mid; else ls = mid + 1;
-    }
-    return ls;
-}
-
 // The same with the (at most 32) components of a short x held in registers, lane c holding
 // component c: its segment start st, length cnt, first chunk ch0 and x's value xv.
 template <bool CREATE, bool FIRST>
@@ -734,7 +720,6 @@ __device__ __forceinline__ void join_class(const JoinParams &P, const int64_t it
                         le = ls + wp[w + 1];
                         ls = ls + wp[w];
                     }
-                    if (lo > 0 && le - ls >= SKIP_MIN) ls = first_after_x(P.post, ls, le, lx, idmask);
                     cnt = (int32_t)(le - ls);
                     st = ls;
                     if (gw == 0) ct.read += (uint32_t)cnt;
@@ -782,10 +767,9 @@ __device__ __forceinline__ void join_class(const JoinParams &P, const int64_t it
                         le = ls + wp[w + 1];
                         ls = ls + wp[w];
                     }
-                    if (lo > 0 && le - ls >= SKIP_MIN) ls = first_after_x(P.post, ls, le, lx, idmask);
                     cnt = (int32_t)(le - ls);
                     st = ls;
-                    ct.read += (uint32_t)cnt;  // every entry of the segment is loaded
+                    ct.read += (uint32_t)cnt;  // every entry of the window's list is loaded
                 }
                 // scan of (chunks, non-empty, non-empty creating) packed in one int64
                 const int64_t nch = (cnt + 127) >> 7;
