@@ -94,6 +94,55 @@ def test_multi_window_instance(aps):
     compare(i, j, s, ref, f32(t), c.n, csr=c)
 
 
+@pytest.mark.parametrize("t", [0.5, 0.8, 0.95])
+@pytest.mark.parametrize("join_flags", [0, 0x10, 0x20, 0x70])
+def test_one_and_two_component_vectors(aps, t, join_flags):
+    """Vectors of one and two components (the streamed class: no accumulator, the two lists
+    of a two-component vector merged by id) over several candidate windows (n > 20480), with
+    dense dimensions so that lists are long, an id shared by both lists is common and
+    two-component vectors often meet a rank in the other vector's unindexed prefix; the
+    pruning toggles (remscore, minsize, upperbound off) change which vectors create."""
+    rng = np.random.default_rng(91)
+    n, m = 30000, 300
+    lengths = rng.integers(1, 3, size=n)
+    c = synth.sparse_vectors(n, m, lengths, 1.0, "lognormal", 91, rng=rng)
+    i, j, s, st = run_join(aps, c, f32(t), 0, join_flags)
+    ref, _ = oracle.all_pairs(c, f32(t), oracle.ALL_PAIRS_2)
+    assert len(ref.i) > 1000
+    compare(i, j, s, ref, f32(t), c.n, csr=c)
+    assert st["visits"] <= st["entries_read"]
+
+
+def test_short_vectors_among_long_ones_on_a_batch(aps):
+    """A batch whose instances mix one- and two-component vectors with long ones: the
+    streamed class and the windowed classes share one launch, each instance's pairs in its
+    own output range."""
+    import torch
+
+    rng = np.random.default_rng(92)
+    sizes = [700, 3000, 25000, 90]
+    parts = []
+    for k, n in enumerate(sizes):
+        lengths = np.where(rng.random(n) < 0.5, rng.integers(1, 3, size=n), rng.integers(3, 60, size=n))
+        parts.append(synth.sparse_vectors(n, 500, lengths, 1.0, "lognormal", 93 + k, rng=rng))
+    ro = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    ip = np.concatenate([[0]] + [p.indptr[1:] + sum(q.nnz for q in parts[:k]) for k, p in enumerate(parts)])
+    ix = np.concatenate([p.idx for p in parts])
+    vv = np.concatenate([p.val for p in parts])
+    ts = np.array([0.6, 0.75, 0.9, 0.5], dtype=np.float32)
+    outs, _ = aps.aps_batch_all_pairs_csr(ro, torch.from_numpy(ip.astype(np.int64)).cuda(),
+                                          torch.from_numpy(ix).cuda(), torch.from_numpy(vv).cuda(),
+                                          np.full(len(sizes), 500, np.int32), ts, 0)
+    try:
+        for k, (p, o) in enumerate(zip(parts, outs)):
+            i, j, s = aps.pairs_to_numpy(o)
+            ref, _ = oracle.all_pairs(p, float(ts[k]), oracle.ALL_PAIRS_2)
+            compare(i, j, s, ref, float(ts[k]), p.n, csr=p)
+    finally:
+        for o in outs:
+            aps.aps_pairs_free(o)
+
+
 @pytest.mark.parametrize(
     "build_flags,join_flags",
     [(0, 0), (8, 0), (0, 0x10), (0, 0x20), (0, 0x40), (0, 0x70), (8, 0x70), (4, 0), (2, 0)],
