@@ -187,9 +187,11 @@ __device__ __forceinline__ double warp_incl_scan_f64(double v, int lane) {
 __global__ void k_split(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
                         const float *__restrict__ cval, const float *__restrict__ mwr,
                         const int32_t *__restrict__ vinst, const InstDesc *__restrict__ inst, int64_t N,
-                        uint32_t flags, int32_t *split, int32_t *qsplit, float *mwpre, float *pnorm) {
+                        uint32_t flags, int32_t *split, int32_t *qsplit, float *mwpre, float *pnorm, int64_t M,
+                        uint64_t *pkeys, uint32_t *pvals, unsigned long long *nsuf) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long nsuf_w = 0;  // this warp's indexed components (lane 0)
     for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < N; x += nwarps) {
         const InstDesc &I = inst[vinst[x]];
         const double t = (double)I.t;
@@ -237,34 +239,17 @@ __global__ void k_split(const int64_t *__restrict__ cptr, const int32_t *__restr
             qsplit[x] = qs;
             mwpre[x] = best;
             pnorm[x] = sp ? __fmul_ru(__fsqrt_ru(pss), 1.0011f) : 0.f;
+            nsuf_w += (unsigned long long)(L - sp);
+        }
+        // the row's posting keys: a suffix entry its global rank, a prefix entry a sentinel
+        // past the last rank (it sorts last); the value is the entry's index. The sort is
+        // stable and entries arrive in row order, so every list comes out in increasing id.
+        for (int64_t p = a + lane; p < b; p += 32) {
+            pkeys[p] = (p - a >= sp) ? (uint64_t)I.rbase + (uint64_t)crank[p] : (uint64_t)M;
+            pvals[p] = (uint32_t)p;
         }
     }
-}
-
-// Suffix entries get their posting-list key (global rank); the unindexed prefix entries
-// get a sentinel past the last rank so they sort last. The sort is stable and entries
-// arrive in row order, so every list comes out in increasing vector id.
-__global__ void k_post_keys(const int64_t *__restrict__ cptr, const int32_t *__restrict__ crank,
-                            const int32_t *__restrict__ erow, const int32_t *__restrict__ split,
-                            const int32_t *__restrict__ vinst, const InstDesc *__restrict__ inst, int64_t nnz,
-                            int64_t M, uint64_t *keys, uint32_t *vals, unsigned long long *nsuf) {
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of 32: warps stay whole
-    // the loop runs while the warp's first entry is in range, so the count below is taken
-    // by whole warps (one atomic per warp instead of one per entry)
-    for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; p0 < nnz; p0 += stride) {
-        const int64_t p = p0 + lane;
-        bool suf = false;
-        if (p < nnz) {
-            const int64_t x = erow[p];
-            const InstDesc &I = inst[vinst[x]];
-            suf = (p - cptr[x]) >= split[x];
-            keys[p] = suf ? (uint64_t)I.rbase + (uint64_t)crank[p] : (uint64_t)M;
-            vals[p] = (uint32_t)p;
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, suf);
-        if (lane == 0 && bal) atomicAdd(nsuf, (unsigned long long)__popc(bal));
-    }
+    if (lane == 0 && nsuf_w) atomicAdd(nsuf, nsuf_w);
 }
 
 __global__ void k_post_fill(const uint32_t *__restrict__ vals, const int32_t *__restrict__ erow,
@@ -350,34 +335,37 @@ __global__ void k_item_keys(const int64_t *__restrict__ cptr, const int32_t *__r
                             const int64_t *__restrict__ lptr, const int32_t *__restrict__ vinst,
                             const InstDesc *__restrict__ inst, int64_t N, uint64_t *keys, uint32_t *vals,
                             unsigned long long *class_count) {
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N; x += (int64_t)gridDim.x * blockDim.x) {
+    // one warp per vector: the lanes read its ranks side by side and look up their lists
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < N; x += nwarps) {
         const InstDesc &I = inst[vinst[x]];
-        int64_t lx = x - I.vbase;
-        uint64_t key;
-        if (lx < (int64_t)I.n - 1) {
-            double later = (double)(I.n - 1 - lx);
-            int64_t lsum = 0;  // total length of x's posting lists (four lookups at a time)
-            const int64_t a = cptr[x], b = cptr[x + 1];
-            for (int64_t p0 = a; p0 < b; p0 += 4) {
-                int64_t l4[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int64_t R = (int64_t)I.rbase + crank[min(p0 + u, b - 1)];
-                    l4[u] = p0 + u < b ? lptr[R + 1] - lptr[R] : 0;
-                }
-                lsum += l4[0] + l4[1] + l4[2] + l4[3];
+        const int64_t lx = x - I.vbase;
+        if (lx >= (int64_t)I.n - 1) {  // no later candidates: after every class
+            if (lane == 0) {
+                keys[x] = (uint64_t)JOIN_NCLS << 24;
+                vals[x] = (uint32_t)x;
             }
-            const double lists = (double)lsum;
-            double cost = lists * later / (double)I.n + later / 8.0 + 32.0;
-            uint64_t c = cost >= 4294967295.0 ? 0xffffffffull : (uint64_t)cost;
-            const int cls = b - a <= 2 ? 4 : I.G == 1 ? 0 : I.G == 2 ? 1 : I.G == 4 ? 2 : 3;
-            key = ((uint64_t)cls << 32) | (0xffffffffull - c);
-            atomicAdd(&class_count[cls], 1ull);
-        } else {
-            key = 5ull << 32;
+            continue;
         }
-        keys[x] = key;
-        vals[x] = (uint32_t)x;
+        const int64_t a = cptr[x], b = cptr[x + 1];
+        int64_t lsum = 0;  // total length of x's posting lists
+        for (int64_t p = a + lane; p < b; p += 32) {
+            const int64_t R = (int64_t)I.rbase + crank[p];
+            lsum += lptr[R + 1] - lptr[R];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        if (lane == 0) {
+            const double later = (double)(I.n - 1 - lx);
+            const double cost = (double)lsum * later / (double)I.n + later / 8.0 + 32.0;
+            // decreasing cost inside the class, in 24 bits (the costliest saturate together)
+            const uint64_t c = cost >= 16777215.0 ? 0xffffffull : (uint64_t)cost;
+            const int cls = b - a <= 2 ? 4 : I.G == 1 ? 0 : I.G == 2 ? 1 : I.G == 4 ? 2 : 3;
+            keys[x] = ((uint64_t)cls << 24) | (0xffffffull - c);
+            vals[x] = (uint32_t)x;
+            atomicAdd(&class_count[cls], 1ull);
+        }
     }
 }
 
@@ -545,21 +533,20 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     }
     // ---- a3: partial-indexing split
     APS_TRY(d.pnorm.alloc((size_t)std::max<int64_t>(N, 1), s));
+    // the split also writes each row's posting keys for a4 (and counts the indexed components)
+    DBuf<uint64_t> pkeys;
+    DBuf<uint32_t> pvals;
+    APS_TRY(pkeys.alloc((size_t)std::max<int64_t>(nnz, 1), s));
+    APS_TRY(pvals.alloc((size_t)std::max<int64_t>(nnz, 1), s));
+    unsigned long long *nsuf_d = err.p + 1;
     k_split<<<grid_for(N * 32, T256), T256, 0, s>>>(d.cptr.p, d.crank.p, d.cval.p, d.mwr.p, d.vinst.p, d.inst.p, N,
-                                                    ix->flags, d.split.p, d.qsplit.p, d.mwpre.p, d.pnorm.p);
+                                                    ix->flags, d.split.p, d.qsplit.p, d.mwpre.p, d.pnorm.p, M,
+                                                    pkeys.p, pvals.p, nsuf_d);
     APS_LAUNCH_CHECK();
     // ---- a4: suffix inverted index
     {
-        DBuf<uint64_t> keys;
-        DBuf<uint32_t> vals;
-        APS_TRY(keys.alloc((size_t)nnz, s));
-        APS_TRY(vals.alloc((size_t)nnz, s));
-        unsigned long long *nsuf_d = err.p + 1;
-        if (nnz > 0) {
-            k_post_keys<<<gE, T256, 0, s>>>(d.cptr.p, d.crank.p, erow.p, d.split.p, d.vinst.p, d.inst.p, nnz, M,
-                                            keys.p, vals.p, nsuf_d);
-            APS_LAUNCH_CHECK();
-        }
+        DBuf<uint64_t> &keys = pkeys;
+        DBuf<uint32_t> &vals = pvals;
         unsigned long long nsuf_h = 0;
         APS_CUDA(cudaMemcpyAsync(&nsuf_h, nsuf_d, sizeof(nsuf_h), cudaMemcpyDeviceToHost, s));
         APS_CUDA(cudaStreamSynchronize(s));
@@ -598,10 +585,11 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
         unsigned long long *cc = err.p;  // reused: one counter per class
         APS_CUDA(cudaMemsetAsync(cc, 0, JOIN_NCLS * sizeof(unsigned long long), s));
         if (N > 0) {
-            k_item_keys<<<gN, T256, 0, s>>>(d.cptr.p, d.crank.p, d.lptr.p, d.vinst.p, d.inst.p, N, keys.p, vals.p,
+            k_item_keys<<<grid_for(N * 32, T256), T256, 0, s>>>(d.cptr.p, d.crank.p, d.lptr.p, d.vinst.p, d.inst.p,
+                                                               N, keys.p, vals.p,
                                             cc);
             APS_LAUNCH_CHECK();
-            APS_TRY(sort_pairs(keys.p, vals.p, N, 35, s));
+            APS_TRY(sort_pairs(keys.p, vals.p, N, 27, s));  // 3 class bits + 24 cost bits
         }
         unsigned long long cnt_h[JOIN_NCLS] = {};
         APS_CUDA(cudaMemcpyAsync(cnt_h, cc, sizeof(cnt_h), cudaMemcpyDeviceToHost, s));
