@@ -335,7 +335,11 @@ __global__ void k_item_keys(const int64_t *__restrict__ cptr, const int32_t *__r
                             const int64_t *__restrict__ lptr, const int32_t *__restrict__ vinst,
                             const InstDesc *__restrict__ inst, int64_t N, uint64_t *keys, uint32_t *vals,
                             unsigned long long *class_count) {
-    // one warp per vector: the lanes read its ranks side by side and look up their lists
+    // one warp per vector: the lanes read its ranks side by side and look up their lists;
+    // the class counts go through shared memory (one global atomic per class and block)
+    __shared__ unsigned long long ccount[JOIN_NCLS];
+    if (threadIdx.x < JOIN_NCLS) ccount[threadIdx.x] = 0ull;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < N; x += nwarps) {
@@ -364,9 +368,11 @@ __global__ void k_item_keys(const int64_t *__restrict__ cptr, const int32_t *__r
             const int cls = b - a <= 2 ? 4 : I.G == 1 ? 0 : I.G == 2 ? 1 : I.G == 4 ? 2 : 3;
             keys[x] = ((uint64_t)cls << 24) | (0xffffffull - c);
             vals[x] = (uint32_t)x;
-            atomicAdd(&class_count[cls], 1ull);
+            atomicAdd(&ccount[cls], 1ull);
         }
     }
+    __syncthreads();
+    if (threadIdx.x < JOIN_NCLS && ccount[threadIdx.x]) atomicAdd(&class_count[threadIdx.x], ccount[threadIdx.x]);
 }
 
 __global__ void k_take_vals(const uint32_t *__restrict__ vals, int64_t n, int32_t *out) {
