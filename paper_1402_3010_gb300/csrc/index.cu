@@ -47,9 +47,11 @@ __global__ void k_validate(const int64_t *__restrict__ indptr, const int32_t *__
                            const float *__restrict__ val, const int32_t *__restrict__ vinst,
                            const InstDesc *__restrict__ inst, int64_t N, int64_t nnz, uint32_t flags,
                            int32_t *__restrict__ erow, float *__restrict__ vout, int32_t *__restrict__ len,
-                           float *__restrict__ mw, unsigned long long *err) {
+                           float *__restrict__ mw, unsigned long long *err,
+                           unsigned long long *longest_out) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long longest = 0;  // the longest row this warp met (to *longest_out, when given)
     for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < N; x += nwarps) {
         const int64_t a = indptr[x], b = indptr[x + 1];
         if (a < 0 || b < a || b > nnz) {
@@ -105,6 +107,74 @@ __global__ void k_validate(const int64_t *__restrict__ indptr, const int32_t *__
             if (code) atomicMin(err, ((unsigned long long)x << 8) | (unsigned long long)code);
             len[x] = (int32_t)(b - a);
             mw[x] = best;
+            longest = max(longest, (unsigned long long)(b - a));
+        }
+    }
+    if (lane == 0 && longest && longest_out) atomicMax(longest_out, longest);
+}
+
+// The rank-ordered rows when no row is longer than 64 components: one warp per row sorts
+// the row's (rank, value) pairs by a bitonic network over the lanes, two per lane (element
+// k = 2 * lane + h), instead of the global sort by (row, rank) that longer rows need.
+__global__ void k_canon_rows64(const int64_t *__restrict__ cptr, const int32_t *__restrict__ idx,
+                               const float *__restrict__ vout, const int32_t *__restrict__ vinst,
+                               const InstDesc *__restrict__ inst, const int32_t *__restrict__ rank_of_dim,
+                               int64_t N, int32_t *crank, float *cval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < N; x += nwarps) {
+        const int64_t a = cptr[x];
+        const int L = (int)(cptr[x + 1] - a);  // <= 64
+        const int64_t rb = inst[vinst[x]].rbase;
+        const int k0 = 2 * lane, k1 = k0 + 1;
+        int r0 = 0x7fffffff, r1 = 0x7fffffff;  // padding sorts last
+        float v0 = 0.f, v1 = 0.f;
+        if (k0 < L) {
+            r0 = rank_of_dim[rb + idx[a + k0]];
+            v0 = vout[a + k0];
+        }
+        if (k1 < L) {
+            r1 = rank_of_dim[rb + idx[a + k1]];
+            v1 = vout[a + k1];
+        }
+#pragma unroll
+        for (int size = 2; size <= 64; size <<= 1) {
+            // blocks of `size` elements ascending where bit `size` of k is 0, descending elsewhere
+            const bool asc = (k0 & size) == 0;  // (k0 and k1 agree on it for size >= 2)
+#pragma unroll
+            for (int j = size >> 1; j > 0; j >>= 1) {
+                if (j == 1) {  // elements k0, k1 of this lane
+                    if ((r0 > r1) == asc) {
+                        const int tr = r0;
+                        r0 = r1;
+                        r1 = tr;
+                        const float tv = v0;
+                        v0 = v1;
+                        v1 = tv;
+                    }
+                } else {  // element k and k ^ j: the same slot of lane ^ (j / 2)
+                    const int lm = j >> 1;
+                    const int p0 = __shfl_xor_sync(0xffffffffu, r0, lm), p1 = __shfl_xor_sync(0xffffffffu, r1, lm);
+                    const float q0 = __shfl_xor_sync(0xffffffffu, v0, lm), q1 = __shfl_xor_sync(0xffffffffu, v1, lm);
+                    const bool keep_min = ((lane & lm) == 0) == asc;  // the lower element keeps the min when ascending
+                    if (keep_min ? p0 < r0 : p0 > r0) {
+                        r0 = p0;
+                        v0 = q0;
+                    }
+                    if (keep_min ? p1 < r1 : p1 > r1) {
+                        r1 = p1;
+                        v1 = q1;
+                    }
+                }
+            }
+        }
+        if (k0 < L) {
+            crank[a + k0] = r0;
+            cval[a + k0] = v0;
+        }
+        if (k1 < L) {
+            crank[a + k1] = r1;
+            cval[a + k1] = v1;
         }
     }
 }
@@ -486,11 +556,12 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     k_vinst<<<gN, T256, 0, s>>>(d.inst.p, k, N, d.vinst.p);
     APS_LAUNCH_CHECK();
     k_validate<<<grid_for(N * 32, T256), T256, 0, s>>>(indptr, idx, val, d.vinst.p, d.inst.p, N, nnz, ix->flags,
-                                                       erow.p, vout.p, d.len.p, d.mw.p, err.p);
+                                                       erow.p, vout.p, d.len.p, d.mw.p, err.p, err.p + 2);
     APS_LAUNCH_CHECK();
-    unsigned long long e_h = ~0ull;
-    APS_CUDA(cudaMemcpyAsync(&e_h, err.p, sizeof(e_h), cudaMemcpyDeviceToHost, s));
+    unsigned long long e3[3] = {~0ull, 0ull, 0ull};  // first error, (unused here), longest row
+    APS_CUDA(cudaMemcpyAsync(e3, err.p, sizeof(e3), cudaMemcpyDeviceToHost, s));
     APS_CUDA(cudaStreamSynchronize(s));
+    const unsigned long long e_h = e3[0], longest_row = e3[2];
     if (e_h != ~0ull) {
         long long row = (long long)(e_h >> 8);
         int code = (int)(e_h & 0xff);
@@ -524,7 +595,11 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
                                            d.mwr.p);
         APS_LAUNCH_CHECK();
     }
-    if (nnz > 0) {
+    if (nnz > 0 && longest_row <= 64) {  // every row sorted inside one warp
+        k_canon_rows64<<<grid_for(N * 32, T256), T256, 0, s>>>(d.cptr.p, idx, vout.p, d.vinst.p, d.inst.p,
+                                                               d.rank_of_dim.p, N, d.crank.p, d.cval.p);
+        APS_LAUNCH_CHECK();
+    } else if (nnz > 0) {  // a global sort by (row, rank)
         DBuf<uint64_t> keys;
         DBuf<uint32_t> vals;
         APS_TRY(keys.alloc((size_t)nnz, s));
@@ -691,7 +766,8 @@ aps_status prepare_queries(const aps_index *ix, const int64_t *qptr, const int32
     APS_CUDA(cudaMemsetAsync(err.p, 0xff, sizeof(unsigned long long), s));
     if (nq > 0) {
         k_validate<<<grid_for((int64_t)nq * 32, T256), T256, 0, s>>>(qptr, qidx, qval, vinst.p, dinst.p, nq, nnz,
-                                                                     flags, erow.p, vout.p, len.p, qa.mw.p, err.p);
+                                                                     flags, erow.p, vout.p, len.p, qa.mw.p, err.p,
+                                                                     nullptr);
         APS_LAUNCH_CHECK();
     }
     unsigned long long e_h = ~0ull;

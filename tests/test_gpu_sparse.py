@@ -357,15 +357,18 @@ def _split_is_valid(cv, mwr, cr, a, b, k, t):
     return ok
 
 
-def test_index_build_steps_match_oracle(aps):
+@pytest.mark.parametrize("hi", [300, 64])
+def test_index_build_steps_match_oracle(aps, hi):
     """a1 statistics, a2 ranks and rank-ordered rows, a3 partial-indexing split and a4
     posting lists, each against the oracle's step: bit-exact, except that the split (whose
     float64 running bound the GPU sums in another association order) may fall elsewhere
     where the bound comes within rounding of t; there it is checked for validity and
-    maximality in exact arithmetic."""
+    maximality in exact arithmetic. hi = 64: no row longer than 64 components, so the
+    rank-ordered rows come from the in-warp sort instead of the global one."""
     import paper_1402_3010_gb300 as A
 
-    c = pl_small(61, n=4000, m=3000)
+    c = pl_small(61, n=4000, m=3000, hi=hi)
+    assert np.diff(c.indptr).max() <= 64 if hi == 64 else np.diff(c.indptr).max() > 64
     t = 0.7
     h = A.aps_build_index(c.indptr, c.idx, c.val, c.n, c.m, t)
     try:
