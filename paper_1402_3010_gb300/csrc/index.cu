@@ -190,6 +190,34 @@ __global__ void k_dimstats(const int32_t *__restrict__ idx, const float *__restr
     }
 }
 
+// The same for a batch of instances of at most DIMSTATS_DIMS dimensions each: one CTA per
+// instance counts in shared memory (shared atomics instead of global ones on 25M
+// dimensions), first the non-zeros, then the maxima, each written out once.
+constexpr int DIMSTATS_DIMS = 56 * 1024;  // 224 KB of 32-bit counters
+__global__ void __launch_bounds__(1024) k_dimstats_inst(const int64_t *__restrict__ cptr,
+                                                        const int32_t *__restrict__ idx,
+                                                        const float *__restrict__ vout,
+                                                        const InstDesc *__restrict__ inst, int32_t *nnz_d,
+                                                        float *mw_d) {
+    extern __shared__ uint32_t dcnt[];  // [I.m]
+    const InstDesc I = inst[blockIdx.x];
+    const int64_t a = cptr[I.vbase], b = cptr[I.vbase + I.n];
+    for (int pass = 0; pass < 2; pass++) {
+        for (int d = threadIdx.x; d < I.m; d += blockDim.x) dcnt[d] = 0u;
+        __syncthreads();
+        for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x) {
+            if (pass == 0) atomicAdd(&dcnt[idx[p]], 1u);
+            else atomicMax(&dcnt[idx[p]], __float_as_uint(vout[p]));  // positive floats order like their bits
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < I.m; d += blockDim.x) {
+            if (pass == 0) nnz_d[(int64_t)I.rbase + d] = (int32_t)dcnt[d];
+            else mw_d[(int64_t)I.rbase + d] = __uint_as_float(dcnt[d]);
+        }
+        __syncthreads();
+    }
+}
+
 // Dimension order of all-pairs-1: decreasing non-zero count; the sort is stable and the
 // input is in id order, so ties keep ascending dimension id.
 __global__ void k_rank_keys(const int32_t *__restrict__ nnz_d, const InstDesc *__restrict__ inst, int k,
@@ -577,7 +605,12 @@ aps_status build_index_device(aps_index *ix, const int64_t *indptr, const int32_
     }
     APS_CUDA(cudaMemsetAsync(d.nnz_d.p, 0, sizeof(int32_t) * M, s));
     APS_CUDA(cudaMemsetAsync(d.mw_d.p, 0, sizeof(float) * M, s));
-    if (nnz > 0) {
+    if (nnz > 0 && k > 1 && maxm <= DIMSTATS_DIMS) {  // a batch of small instances: one CTA each
+        const int sm = (int)(sizeof(uint32_t) * (size_t)maxm);
+        APS_CUDA(cudaFuncSetAttribute(k_dimstats_inst, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        k_dimstats_inst<<<k, 1024, sm, s>>>(d.cptr.p, idx, vout.p, d.inst.p, d.nnz_d.p, d.mw_d.p);
+        APS_LAUNCH_CHECK();
+    } else if (nnz > 0) {
         k_dimstats<<<gE, T256, 0, s>>>(idx, vout.p, erow.p, d.vinst.p, d.inst.p, nnz, d.nnz_d.p, d.mw_d.p);
         APS_LAUNCH_CHECK();
     }
