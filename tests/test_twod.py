@@ -91,7 +91,7 @@ def check(msgs, t, seed=3, failed=()):
     compare(i, j, s, ref, t, c.n, csr=c)
 
 
-@pytest.mark.parametrize("p,q", [(2, 2), (2, 1), (4, 2)])
+@pytest.mark.parametrize("p,q", [(1, 1), (2, 2), (2, 1), (4, 2)])
 def test_twod_matches_whole_set(p, q):
     t = float(np.float32(0.6))
     check(run(p, q, t=t), t)
